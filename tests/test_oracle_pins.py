@@ -1,0 +1,432 @@
+"""Pins for the FP64 CPU oracle against things the paper and mathematics fix.
+
+Each test pins the oracle to something other than itself: hand-computed
+vectors, published generator outputs, closed-form LPs, brute-force vertex
+enumeration, an independent LP solver (HiGHS via scipy), LP duality and the
+firm nonexpansiveness of the PDHG operator.  ``test_planted_mistakes_are_caught``
+plants known mistakes in the oracle and checks that some pin fails for each.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lpgen
+
+INF = np.inf
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _f(v):
+    return float(v) if not isinstance(v, str) else float(v.replace("inf", "inf"))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3 primitives: hand-computed vectors
+# ---------------------------------------------------------------------------
+
+def test_projection_hand_vectors(oracle_lib):
+    o = oracle_lib
+    v = [-3.0, 0.5, 7.0, -2.0, 4.0, -1.0, 2.0]
+    a = [-1.0, 0.0, 1.0, -INF, -INF, 0.0, -INF]
+    b = [1.0, 1.0, 5.0, 3.0, INF, INF, INF]
+    np.testing.assert_array_equal(o.project_box(v, a, b), [-1.0, 0.5, 5.0, -2.0, 4.0, 0.0, 2.0])
+    # barrier cone: v >= 0 where a=-inf, v <= 0 where b=+inf, {0} where both infinite
+    np.testing.assert_array_equal(o.project_barrier(v, a, b), [-3.0, 0.5, 7.0, 0.0, 0.0, -1.0, 0.0])
+    # recession cone: {0} for finite intervals, R_- for (-inf,b], R_+ for [a,inf), R for R
+    np.testing.assert_array_equal(o.project_recession(v, a, b), [0.0, 0.0, 0.0, -2.0, 4.0, 0.0, 2.0])
+
+
+def test_support_function_hand_values(oracle_lib):
+    o = oracle_lib
+    # phi_[a,b](v) = b^T v_+ + a^T v_-, with 0 * inf = 0
+    assert o.support([2.0, -3.0, 0.0, 1.5], [-1.0, 2.0, -INF, -INF], [4.0, 5.0, 7.0, 3.0]) == 6.5
+    assert o.support([0.0, 0.0], [-INF, -INF], [INF, INF]) == 0.0
+    assert o.support([-1.0], [-INF], [3.0]) == INF  # v outside the barrier cone
+    assert o.support([1.0], [0.0], [INF]) == INF
+
+
+def test_splitmix64_published_outputs(oracle_lib):
+    # SplitMix64 seeded with 0 (Steele, Lea, Flood 2014; reference code by Vigna)
+    assert oracle_lib.splitmix64_at(0, 0) == 0xE220A8397B1DCDAF
+    assert oracle_lib.splitmix64_at(0, 1) == 0x6E789E6AA1B965F4
+    assert oracle_lib.splitmix64_at(0, 2) == 0x06C45D188009454F
+
+
+def test_kkt_handworked_golden(oracle_lib):
+    g = json.load(open(os.path.join(HERE, "golden", "kkt_handworked.json")))
+    lpd = g["lp"]
+    for case in g["cases"]:
+        lp = lpgen.from_dense(lpd["A"], lpd["c"], [_f(v) for v in lpd["row_lo"]],
+                              [_f(v) for v in lpd["row_hi"]], [_f(v) for v in case["var_lo"]],
+                              [_f(v) for v in case["var_hi"]])
+        k = oracle_lib.kkt(lp, 0, 0, 0.0, 0.0, 1.0, case["x"], case["y"])
+        for key in ("obj", "dual_obj", "rel_primal", "rel_dual", "rel_gap"):
+            want = _f(case[key])
+            if math.isinf(want):
+                assert k[key] == want, (case["name"], key)
+            else:
+                assert k[key] == pytest.approx(want, abs=1e-14, rel=1e-12), (case["name"], key)
+
+
+# ---------------------------------------------------------------------------
+# ||A||_2 and scaling
+# ---------------------------------------------------------------------------
+
+def test_norm_estimate_matches_svd(oracle_lib):
+    for seed in range(4):
+        lp = lpgen.random_lp(seed, 12 + seed, 9 + 2 * seed, density=0.4)
+        est, it = oracle_lib.norm2_estimate(lp)
+        exact = np.linalg.norm(lp.dense(), 2)
+        assert est == pytest.approx(exact, rel=1e-7), (seed, it)
+        assert est <= exact * (1 + 1e-12)  # Rayleigh quotient never overshoots
+
+
+def test_ruiz_diagonal_closed_form(oracle_lib):
+    d = np.array([4.0, 0.25, 9.0])
+    lp = lpgen.from_dense(np.diag(d), np.ones(3), -np.ones(3), np.ones(3), -np.ones(3), np.ones(3))
+    dr, dc = oracle_lib.scaling(lp, ruiz_iters=1, pock_chambolle=False)
+    np.testing.assert_allclose(dr, 1 / np.sqrt(d), rtol=1e-15)
+    np.testing.assert_allclose(dc, 1 / np.sqrt(d), rtol=1e-15)
+    # Pock-Chambolle on the identity leaves it unchanged
+    dr2, dc2 = oracle_lib.scaling(lp, ruiz_iters=1, pock_chambolle=True)
+    np.testing.assert_allclose(dr2 * d * dc2, np.ones(3), rtol=1e-15)
+
+
+def test_ruiz_fixed_point_unit_inf_norms(oracle_lib):
+    lp = lpgen.random_lp(3, 15, 11, density=0.5)
+    dr, dc = oracle_lib.scaling(lp, ruiz_iters=60, pock_chambolle=False)
+    a = np.abs(dr[:, None] * lp.dense() * dc[None, :])
+    np.testing.assert_allclose(a.max(axis=1), 1.0, atol=1e-6)
+    np.testing.assert_allclose(a.max(axis=0), 1.0, atol=1e-6)
+
+
+def test_zero_rows_and_columns_keep_unit_scale(oracle_lib):
+    a = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 8.0]])
+    lp = lpgen.from_dense(a, [1, 1, 1], [-1, -1], [1, 1], [0, 0, 0], [1, 1, 1])
+    dr, dc = oracle_lib.scaling(lp)
+    assert dr[0] == 1.0 and dc[1] == 1.0
+
+
+# ---------------------------------------------------------------------------
+# PDHG operator: firm nonexpansiveness in the M-norm (reading R4, minus sign)
+# ---------------------------------------------------------------------------
+
+def _t_data(seed):
+    lp = lpgen.random_lp(seed, 7, 9, density=0.5)
+    est = np.linalg.norm(lp.dense(), 2)
+    return lp, 0.998 / est
+
+
+def test_T_is_nonexpansive_in_M_norm(oracle_lib):
+    o = oracle_lib
+    rng = np.random.default_rng(0)
+    for seed in range(5):
+        lp, eta = _t_data(seed)
+        for w in (0.3, 1.0, 4.0):
+            tau, sigma = eta / w, eta * w
+            for _ in range(40):
+                z1 = rng.normal(size=lp.n) * 3, rng.normal(size=lp.m) * 3
+                z2 = rng.normal(size=lp.n) * 3, rng.normal(size=lp.m) * 3
+                t1 = o.apply_T(lp, lp.c, lp.var_lo, lp.var_hi, lp.row_lo, lp.row_hi, tau, sigma, *z1)
+                t2 = o.apply_T(lp, lp.c, lp.var_lo, lp.var_hi, lp.row_lo, lp.row_hi, tau, sigma, *z2)
+                before = o.mnorm2(lp, w, eta, -1.0, z1[0] - z2[0], z1[1] - z2[1])
+                after = o.mnorm2(lp, w, eta, -1.0, t1[0] - t2[0], t1[1] - t2[1])
+                assert before > 0
+                assert after <= before * (1 + 1e-12) + 1e-12
+
+
+def test_fixed_point_residual_zero_at_optimum(oracle_lib):
+    """At a primal-dual optimum z*, T(z*) = z* (hand LP of the KKT golden)."""
+    o = oracle_lib
+    lp = lpgen.from_dense([[1.0, 2.0]], [1.0, 1.0], [2.0], [INF], [0, 0], [10, 10])
+    x, y = np.array([0.0, 1.0]), np.array([-0.5])
+    for tau, sigma in ((0.1, 0.3), (0.4, 0.2)):
+        xh, yh = o.apply_T(lp, lp.c, lp.var_lo, lp.var_hi, lp.row_lo, lp.row_hi, tau, sigma, x, y)
+        np.testing.assert_allclose(xh, x, atol=1e-15)
+        np.testing.assert_allclose(yh, y, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# whole-solver pins
+# ---------------------------------------------------------------------------
+
+def highs_solve(lp, specs, q):
+    from scipy.optimize import linprog
+    a = lp.dense()
+    xl, xu, c = lp.var_lo.copy(), lp.var_hi.copy(), lp.c.copy()
+    j = int(specs.var[q])
+    if specs.kind[q] == lpgen.KIND_BOUND:
+        xl[j] = max(xl[j], specs.lo[q])
+        xu[j] = min(xu[j], specs.hi[q])
+    elif specs.kind[q] == lpgen.KIND_OBJECTIVE:
+        c = np.zeros(lp.n)
+        c[j] = specs.sign[q]
+    fu, fl = np.isfinite(lp.row_hi), np.isfinite(lp.row_lo)
+    aub = np.vstack([a[fu], -a[fl]]) if lp.m else None
+    bub = np.concatenate([lp.row_hi[fu], -lp.row_lo[fl]]) if lp.m else None
+    if bub is not None and bub.size == 0:
+        aub = bub = None
+    bounds = [(None if np.isinf(l) else l, None if np.isinf(u) else u) for l, u in zip(xl, xu)]
+    r = linprog(c, A_ub=aub, b_ub=bub, bounds=bounds, method="highs")
+    return r.status, (r.fun if r.status == 0 else None)
+
+
+def test_box_lp_closed_form(oracle_lib):
+    rng = np.random.default_rng(1)
+    n = 9
+    lo = rng.uniform(-5, 0, n)
+    hi = lo + rng.uniform(0.5, 4, n)
+    c = rng.normal(size=n)
+    lp = lpgen.from_dense(np.zeros((0, n)), c, [], [], lo, hi)
+    r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-10, max_iter=10000, check_every=8)
+    assert r.status[0] == 0
+    np.testing.assert_allclose(r.x[0], np.where(c > 0, lo, hi), atol=1e-9)
+    assert r.obj[0] == pytest.approx(np.minimum(c * lo, c * hi).sum(), abs=1e-9)
+    # OBBT on a box returns the box
+    cand = np.arange(n)
+    ro = oracle_lib.solve(lp, lpgen.obbt_specs(cand), tol=1e-10, max_iter=10000, check_every=8)
+    np.testing.assert_allclose(ro.obj[:n], lo, atol=1e-8)
+    np.testing.assert_allclose(-ro.obj[n:], hi, atol=1e-8)
+
+
+def test_continuous_knapsack_closed_form(oracle_lib):
+    rng = np.random.default_rng(2)
+    n = 8
+    a = rng.uniform(0.5, 3, n)
+    c = rng.uniform(0.5, 3, n)
+    u = rng.uniform(0.5, 2, n)
+    b = 0.55 * (a * u).sum()
+    # greedy: cheapest cost per unit of coverage first
+    f, need = 0.0, b
+    for i in np.argsort(c / a):
+        take = min(u[i], need / a[i])
+        f += c[i] * take
+        need -= a[i] * take
+        if need <= 0:
+            break
+    lp = lpgen.from_dense(a[None, :], c, [b], [INF], np.zeros(n), u)
+    r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-9, max_iter=200000, check_every=16)
+    assert r.status[0] == 0
+    assert r.obj[0] == pytest.approx(f, rel=1e-7)
+
+
+def brute_force_vertices(a, c, l, u, xl, xu):
+    """min c^T x over the polytope, by enumerating all vertices: choose n
+    active hyperplanes among {row at l or u, variable at its lower or upper
+    bound}, solve, keep the feasible points.  Returns None when no vertex is
+    feasible (the box is bounded, so the LP is then infeasible)."""
+    m, n = a.shape
+    planes = []
+    for i in range(m):
+        planes.append((a[i], l[i]))
+        planes.append((a[i], u[i]))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        planes.append((e, xl[j]))
+        planes.append((e, xu[j]))
+    best = None
+    for comb in itertools.combinations(range(len(planes)), n):
+        mat = np.array([planes[k][0] for k in comb])
+        if abs(np.linalg.det(mat)) < 1e-10:
+            continue
+        x = np.linalg.solve(mat, np.array([planes[k][1] for k in comb]))
+        ax = a @ x
+        if np.all(ax >= l - 1e-9) and np.all(ax <= u + 1e-9) and np.all(x >= xl - 1e-9) and np.all(x <= xu + 1e-9):
+            f = c @ x
+            best = f if best is None else min(best, f)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_brute_force_vertex_enumeration(oracle_lib, seed):
+    rng = np.random.default_rng(100 + seed)
+    m, n = 2 + seed % 3, 3 + seed % 3
+    a = np.round(rng.uniform(-3, 3, (m, n)), 1)
+    x0 = rng.uniform(0, 1, n)
+    xl, xu = np.zeros(n), np.ones(n)
+    l = a @ x0 - rng.uniform(0, 0.3, m)
+    u = a @ x0 + rng.uniform(0, 0.3, m)
+    if seed % 4 == 3:  # make it infeasible: a row range out of reach
+        l[0] = u[0] = np.abs(a[0]).sum() + 1.0
+    c = rng.normal(size=n)
+    f = brute_force_vertices(a, c, l, u, xl, xu)
+    lp = lpgen.from_dense(a, c, l, u, xl, xu)
+    r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-9, max_iter=400000, check_every=16)
+    if f is None:
+        assert r.status[0] == 1  # PRIMAL_INFEASIBLE
+    else:
+        assert r.status[0] == 0
+        assert r.obj[0] == pytest.approx(f, abs=1e-6 * (1 + abs(f)))
+
+
+def test_sb_small_against_highs(oracle_lib):
+    w = lpgen.sb_small()
+    r = oracle_lib.solve(w.lp, w.specs, tol=1e-8, max_iter=200000)
+    for q in range(len(w.specs)):
+        st, f = highs_solve(w.lp, w.specs, q)
+        assert st == 0 and r.status[q] == 0
+        assert abs(r.obj[q] - f) / (1 + abs(f)) <= 1e-7, q
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_mixed_bound_lps_against_highs(oracle_lib, seed):
+    lp = lpgen.random_lp(seed, 4 + seed % 5, 6 + seed % 4)
+    sp = lpgen.base_specs(1)
+    r = oracle_lib.solve(lp, sp, tol=1e-8, max_iter=400000, check_every=16)
+    st, f = highs_solve(lp, sp, 0)
+    assert r.status[0] == {0: 0, 2: 1, 3: 2}[st]  # HiGHS optimal / infeasible / unbounded
+    if st == 0:
+        assert abs(r.obj[0] - f) / (1 + abs(f)) <= 1e-6
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_infeasibility_status_against_highs(oracle_lib, seed):
+    lp = lpgen.random_lp(seed, 5, 7, feasible=False)
+    sp = lpgen.base_specs(1)
+    r = oracle_lib.solve(lp, sp, tol=1e-6, max_iter=200000, check_every=16)
+    st, f = highs_solve(lp, sp, 0)
+    want = {0: 0, 2: 1, 3: 2}[st]  # HiGHS optimal / infeasible / unbounded
+    assert r.status[0] == want
+    if want == 0:
+        assert abs(r.obj[0] - f) / (1 + abs(f)) <= 1e-4
+
+
+def test_hand_infeasible_and_unbounded(oracle_lib):
+    lp = lpgen.from_dense([[1, 1]], [1, 1], [3], [INF], [0, 0], [1, 1])
+    assert oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-6, check_every=16).status[0] == 1
+    lp = lpgen.from_dense([[1, -1]], [-1, 0], [-INF], [1], [0, 0], [INF, INF])
+    assert oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-6, check_every=16).status[0] == 2
+
+
+def test_complementary_slackness_sign_of_y(oracle_lib):
+    """y_i > 0 only on rows at their upper bound, y_i < 0 only at the lower
+    bound (y in the barrier cone of [l,u], Sec. 3)."""
+    w = lpgen.sb_small()
+    r = oracle_lib.solve(w.lp, w.specs.subset([0]), tol=1e-9, max_iter=300000)
+    x, y = r.x[0], r.y[0]
+    ax = w.lp.matvec(x)
+    scale = np.abs(y).max()
+    up = y > 1e-5 * scale
+    dn = y < -1e-5 * scale
+    assert up.any() and dn.any()
+    np.testing.assert_allclose(ax[up], w.lp.row_hi[up], atol=1e-5)
+    np.testing.assert_allclose(ax[dn], w.lp.row_lo[dn], atol=1e-5)
+
+
+def test_strong_branching_children_not_below_parent(oracle_lib):
+    w = lpgen.sb_small()
+    parent = oracle_lib.solve(w.lp, lpgen.base_specs(1), tol=1e-8, max_iter=200000)
+    kids = oracle_lib.solve(w.lp, w.specs, tol=1e-8, max_iter=200000)
+    assert np.all(kids.obj >= parent.obj[0] - 1e-6 * (1 + abs(parent.obj[0])))
+
+
+def test_obbt_sandwich(oracle_lib):
+    lp = lpgen.random_lp(5, 6, 8, density=0.5)
+    cand = np.arange(lp.n)
+    r = oracle_lib.solve(lp, lpgen.obbt_specs(cand), tol=1e-8, max_iter=400000, check_every=16)
+    ok = r.status == 0
+    lo, hi = r.obj[: lp.n], -r.obj[lp.n:]
+    for j in range(lp.n):
+        if ok[j]:
+            assert lo[j] <= lp.x0[j] + 1e-5
+            assert lo[j] >= lp.var_lo[j] - 1e-5
+        if ok[lp.n + j]:
+            assert hi[j] >= lp.x0[j] - 1e-5
+            assert hi[j] <= lp.var_hi[j] + 1e-5
+
+
+def test_batch_invariance_lockstep_vs_alone(oracle_lib):
+    w = lpgen.sb_small()
+    a = oracle_lib.solve(w.lp, w.specs, tol=1e-8, max_iter=200000, lockstep=1)
+    b = oracle_lib.solve(w.lp, w.specs, tol=1e-8, max_iter=200000, lockstep=0, threads=4)
+    np.testing.assert_array_equal(a.status, b.status)
+    np.testing.assert_allclose(a.obj, b.obj, rtol=1e-6)
+
+
+def test_threads_do_not_change_results(oracle_lib):
+    w = lpgen.sb_small()
+    a = oracle_lib.solve(w.lp, w.specs, tol=1e-6, max_iter=200000, threads=1)
+    b = oracle_lib.solve(w.lp, w.specs, tol=1e-6, max_iter=200000, threads=4)
+    np.testing.assert_array_equal(a.obj, b.obj)
+    np.testing.assert_array_equal(a.iters, b.iters)
+
+
+def test_empty_box_override_is_infeasible_at_zero_iterations(oracle_lib):
+    w = lpgen.sb_small()
+    sp = lpgen.make_specs([1, 0], [3, 0], [5.0, -INF], [4.0, INF])
+    r = oracle_lib.solve(w.lp, sp, tol=1e-4, max_iter=100000)
+    assert r.status[0] == 1 and r.iters[0] == 0
+    assert r.status[1] == 0
+
+
+def test_iteration_limit(oracle_lib):
+    w = lpgen.sb_small()
+    r = oracle_lib.solve(w.lp, w.specs.subset([0, 1]), tol=1e-12, max_iter=1)
+    assert np.all(r.status == 3) and np.all(r.iters == 1)
+
+
+def test_scaling_does_not_change_the_optimum(oracle_lib):
+    w = lpgen.sb_small()
+    sp = w.specs.subset([0, 9])
+    a = oracle_lib.solve(w.lp, sp, tol=1e-8, max_iter=300000)
+    b = oracle_lib.solve(w.lp, sp, tol=1e-8, max_iter=300000, ruiz_iters=0, pock_chambolle=0)
+    np.testing.assert_allclose(a.obj, b.obj, rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes
+# ---------------------------------------------------------------------------
+
+def _pins_pass(o, mutation):
+    """A fast subset of the pins; False as soon as one fails under `mutation`."""
+    try:
+        # hand KKT golden
+        o.set_mutation(mutation)
+        g = json.load(open(os.path.join(HERE, "golden", "kkt_handworked.json")))
+        lpd = g["lp"]
+        for case in g["cases"][:4]:
+            lp = lpgen.from_dense(lpd["A"], lpd["c"], [_f(v) for v in lpd["row_lo"]],
+                                  [_f(v) for v in lpd["row_hi"]], [_f(v) for v in case["var_lo"]],
+                                  [_f(v) for v in case["var_hi"]])
+            k = o.kkt(lp, 0, 0, 0.0, 0.0, 1.0, case["x"], case["y"])
+            for key in ("obj", "dual_obj", "rel_primal", "rel_dual", "rel_gap"):
+                if abs(k[key] - _f(case[key])) > 1e-12:
+                    return False
+        # nonexpansiveness on one LP
+        lp, eta = _t_data(0)
+        rng = np.random.default_rng(0)
+        for w in (0.3, 4.0):
+            for _ in range(30):
+                z1 = rng.normal(size=lp.n) * 3, rng.normal(size=lp.m) * 3
+                z2 = rng.normal(size=lp.n) * 3, rng.normal(size=lp.m) * 3
+                t1 = o.apply_T(lp, lp.c, lp.var_lo, lp.var_hi, lp.row_lo, lp.row_hi, eta / w, eta * w, *z1)
+                t2 = o.apply_T(lp, lp.c, lp.var_lo, lp.var_hi, lp.row_lo, lp.row_hi, eta / w, eta * w, *z2)
+                if o.mnorm2(lp, w, eta, -1.0, t1[0] - t2[0], t1[1] - t2[1]) > \
+                        o.mnorm2(lp, w, eta, -1.0, z1[0] - z2[0], z1[1] - z2[1]) * (1 + 1e-12) + 1e-12:
+                    return False
+        o.set_mutation(0)
+        # HiGHS on two random LPs, through the solver with the mutation planted
+        for seed in (1, 2):
+            lp = lpgen.random_lp(seed, 5, 7)
+            sp = lpgen.base_specs(1)
+            r = o.solve(lp, sp, tol=1e-7, max_iter=30000, check_every=16, mutation=mutation)
+            st, f = highs_solve(lp, sp, 0)
+            if r.status[0] != 0 or abs(r.obj[0] - f) / (1 + abs(f)) > 1e-5:
+                return False
+        return True
+    finally:
+        o.set_mutation(0)
+
+
+def test_pins_pass_without_mutation(oracle_lib):
+    assert _pins_pass(oracle_lib, 0)
+
+
+@pytest.mark.parametrize("mutation", range(1, 8))
+def test_planted_mistakes_are_caught(oracle_lib, mutation):
+    assert not _pins_pass(oracle_lib, mutation)
