@@ -1,0 +1,354 @@
+"""Benchmark: LPs solved per second by the batched PDHG solver on one GB300.
+
+A step is one complete batched solve (every LP of the batch to rel-KKT 1e-4,
+all hot-path steps: both fused SpMM steps, FP64 checks, restarts,
+compaction) of a seeded synthetic batch whose matrix is already resident on
+the GPU.  The default workload is 64 strong-branching children of a shared
+A with m=20k, n=50k and power-law row lengths (nnz ~ 250k), FP32 iterates
+with FP64 checks.
+
+Prints ONE JSON line (rank 0).  Under torchrun with N>1 every rank solves
+its own, independently seeded batch (weak scaling, no collective on the data
+path); value = LPs solved by all ranks / max-over-ranks time.
+
+--impl reference times the CPU oracle (plain FP64 C, all host cores) on a
+bounded sample of the same workload; it is the slow reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lpgen  # noqa: E402
+
+METRIC = "LPs solved/s to rel-KKT 1e-4 (batched vs B=1 loop); SpMM HBM GB/s; p99 lat"
+UNIT = "LPs/s"
+TOL = 1e-4
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "sb_powerlaw": dict(fn=lambda seed: lpgen.sb_powerlaw(seed=seed), max_iter=100000),
+    "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000),
+    "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000),
+    "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def solved(res) -> int:
+    st = res["status"]
+    return int(np.sum((st == 0) | (st == 1) | (st == 2)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lpb_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic(kernel_name: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2601_21990_gb300", "csrc", "lpb_iter.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(workload, {}).get(kernel_name)
+    if not ent or ent.get("lpb_iter_sha") != h:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on the host cores: a bounded sample."""
+    if world > 1 and rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    w = WORKLOADS[args.workload]["fn"](args.seed)
+    q = len(w.specs)
+    sample = min(q, args.ref_lps)
+    sp = w.specs.subset(range(sample))
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup if args.ref_warmup else 0):
+        oracle.solve(w.lp, sp, tol=TOL, max_iter=WORKLOADS[args.workload]["max_iter"], threads=cores,
+                     lockstep=0, want_xy=False)
+    times, nsolved = [], 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle.solve(w.lp, sp, tol=TOL, max_iter=WORKLOADS[args.workload]["max_iter"], threads=cores,
+                         lockstep=0, want_xy=False)
+        times.append(time.perf_counter() - t)
+        nsolved += int(np.sum(r.status <= 2))
+    total = sum(times)
+    v = nsolved / total
+    desc = f"{sample} of {q} LPs of {w.name}, each solved alone (own restarts), OpenMP over LPs"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "tol": TOL, "sample_lps": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(w, cores, budget_lps):
+    import oracle
+
+    oracle.build()
+    q = len(w.specs)
+    sample = min(q, budget_lps)
+    sp = w.specs.subset(range(sample))
+    t = time.perf_counter()
+    r = oracle.solve(w.lp, sp, tol=TOL, max_iter=100000, threads=cores, lockstep=0, want_xy=False)
+    dt = time.perf_counter() - t
+    return {"value": int(np.sum(r.status <= 2)) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample} of {q} LPs of {w.name}, each alone, OpenMP over LPs, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sb_powerlaw", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ref-lps", type=int, default=64)
+    ap.add_argument("--ref-warmup", action="store_true")
+    ap.add_argument("--cpu-lps", type=int, default=64, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--b1-lps", type=int, default=8, help="LPs solved one at a time for the B=1 comparison")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2601_21990_gb300 import lpb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # each rank: its own seeded batch (weak scaling)
+    w = WORKLOADS[args.workload]["fn"](args.seed + rank)
+    max_iter = WORKLOADS[args.workload]["max_iter"]
+    precision = lpb.FP64 if w.precision == "fp64" else lpb.MIXED
+    opts = lpb.lpb_default_options(precision=precision, profile=1, device=local, cuda_stream=stream.cuda_stream)
+    h = lpb.Handle(w.lp, options=opts)
+    specs_np = lpb.specs_from(w.specs)
+    specs_dev = torch.from_numpy(specs_np.view(np.uint8).copy()).to(dev)
+    q = len(w.specs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        b = h.solve_dev(specs_dev, tol=TOL, max_iter=max_iter)
+        res = b.results()
+        prof = b.profile()
+        b.free()
+        return res, prof
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    nsolved, profs, lat = 0, [], []
+    torch.cuda.nvtx.range_push("timed")
+    for k in range(args.steps):
+        flush.zero_()  # L2 (129 MB) flushed between timed solves
+        ev[k][0].record(stream)
+        res, prof = one_step()
+        ev[k][1].record(stream)
+        nsolved += solved(res)
+        profs.append(prof)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        cnt = torch.tensor([nsolved], device=dev, dtype=torch.float64)
+        dist.all_reduce(cnt)
+        nsolved_all = int(cnt.item())
+    else:
+        nsolved_all = nsolved
+    value = nsolved_all / (total_ms / 1e3)
+
+    # roofline of the dominant kernel, from the library's CUDA events on this stream
+    ms = np.array([[p.ms[i] for i in range(4)] for p in profs]).sum(0)
+    by = np.array([[p.bytes[i] for i in range(4)] for p in profs]).sum(0)
+    la = np.array([[p.launches[i] for i in range(4)] for p in profs]).sum(0)
+    names = ["k_primal (A~^T Y + primal step)", "k_dual (A~ Xbar + dual step)"]
+    dom = int(np.argmax(ms[:2]))
+    achieved = by[dom] / (ms[dom] / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = ncu_traffic(["k_primal", "k_dual"][dom], args.workload)
+    gpu_launches = int(sum(p.kernels for p in profs))
+
+    # B=1 loop: the same kernels, one LP per solve
+    b1_n = min(args.b1_lps, q)
+    b1_specs = [torch.from_numpy(specs_np[i:i + 1].view(np.uint8).copy()).to(dev) for i in range(b1_n)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b1_solved = 0
+    for i in range(b1_n):
+        b = h.solve_dev(b1_specs[i], tol=TOL, max_iter=max_iter)
+        b1_solved += solved(b.results())
+        b.free()
+    torch.cuda.synchronize()
+    b1_s = time.perf_counter() - t0
+    b1_value = b1_solved / b1_s
+
+    # end to end through the public host API: create (H2D of A, vectors),
+    # solve from host records, results back to the host
+    lp = w.lp
+    h2d = (lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.vals.nbytes + lp.c.nbytes + lp.row_lo.nbytes +
+           lp.row_hi.nbytes + lp.var_lo.nbytes + lp.var_hi.nbytes + specs_np.nbytes)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_solved, d2h = 0, 0
+    for _ in range(e2e_steps):
+        he = lpb.Handle(lp, precision=precision, device=local)
+        be = he.solve(specs_np, tol=TOL, max_iter=max_iter)
+        r = be.results()
+        d2h = r.nbytes
+        e2e_solved += solved(r)
+        be.free()
+        he.close()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e2e_solved / e2e_s * (world if dist else 1)
+
+    out = None
+    if rank == 0:
+        cores = os.cpu_count() or 1
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, cores, args.cpu_lps)
+        setup_ms = profs[0].setup_ms if profs else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == lpb.FP64 else "f32-iterates/f64-checks", "data": "synthetic",
+            "config": {"workload": w.name, "m": lp.m, "n": lp.n, "nnz": lp.nnz, "lps_per_step": q, "tol": TOL,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MB write)",
+                       "lps_solved_per_step": nsolved / args.steps},
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic, "launches": int(la[dom]),
+                         "avg_launch_us": 1e3 * ms[dom] / max(la[dom], 1),
+                         "other_kernel_GBps": by[1 - dom] / (ms[1 - dom] / 1e3) / 1e9 if ms[1 - dom] > 0 else None},
+            "time_split_ms_per_step": {"primal_step": ms[0] / args.steps, "dual_step": ms[1] / args.steps,
+                                       "check_spmm": ms[2] / args.steps, "check_reduce": ms[3] / args.steps},
+            "b1_loop": {"value": b1_value, "unit": UNIT, "lps": b1_n, "batched_over_b1": value / world / b1_value},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "what": "one batched solve"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "what": "lpb_create from host CSR + lpb_solve from host records + lpb_results"},
+            "gpu_launches": gpu_launches,
+            "setup_ms": setup_ms,
+            "clocks": clk,
+        }
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * lpb.h -- C ABI of the batched PDHG LP solver for NVIDIA GB300 (sm_103a).
+ *
+ * Solves many linear programs that share one sparse constraint matrix A
+ * ("Batched First-Order Methods for Parallel LP Solving in MIP", Sec. 3-5):
+ *
+ *     min  c_q^T x   s.t.   l <= A x <= u,   xlo_q <= x <= xhi_q,   q = 1..N
+ *
+ * where LP q differs from the base LP only by one override record: a bound
+ * change on one variable (strong branching, Sec. 5.1) or an objective +-e_j
+ * (optimization-based bound tightening, Sec. 5.2).  The method is restarted
+ * reflected-Halpern PDHG (Sec. 4, Eq. mainiter) run on the whole batch at
+ * once (Sec. 5, Eq. batched_iter) with per-LP step sizes, a batch-averaged
+ * restart test, relative KKT termination (Eq. stopping), infeasibility
+ * detection (Eq. primal-infeas, dual-infeas) and compaction of finished LPs.
+ *
+ * Conventions for every entry point:
+ *  - Pointers without a _dev suffix are HOST pointers.  Inputs are copied
+ *    during the call; the caller keeps ownership and may free them after.
+ *  - Infinite bounds are +-HUGE_VAL (IEEE infinity).
+ *  - Indices are 0-based.  CSR row_ptr has m+1 entries, row_ptr[0] == 0.
+ *  - Every function returns an lpb_err; the library never aborts, traps or
+ *    prints.  lpb_last_error() gives a message for the calling thread.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - All device work of a handle runs on the stream given in lpb_options
+ *    (NULL: a stream the handle creates and owns).
+ */
+#ifndef LPB_H
+#define LPB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lpb_ctx* lpb_handle;     /* one A plus base c, l, u, xlo, xhi on the device */
+typedef struct lpb_batch* lpb_batch_t;  /* the results of one lpb_solve */
+
+typedef enum {
+    LPB_OK = 0,
+    LPB_ERR_INVALID_ARG = 1,   /* bad size, pointer, NaN/Inf data, l > u, unsorted row_ptr ... */
+    LPB_ERR_OOM = 2,           /* device or pinned host allocation failed */
+    LPB_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    LPB_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    LPB_ERR_DEVICE_CHECK = 5,  /* a kernel's own bounds check fired */
+    LPB_ERR_BAD_INDEX = 6      /* an override names a variable outside [0, n) */
+} lpb_err;
+
+typedef enum {
+    LPB_OPTIMAL = 0,           /* rel. primal, dual and gap residuals <= tol (Eq. stopping) */
+    LPB_PRIMAL_INFEASIBLE = 1, /* Eq. primal-infeas held, or the override emptied the box */
+    LPB_DUAL_INFEASIBLE = 2,   /* Eq. dual-infeas held (the LP is unbounded if feasible) */
+    LPB_ITERATION_LIMIT = 3,   /* max_iter reached; the result is the last evaluated point */
+    LPB_NUMERICAL = 4          /* a NaN appeared in the LP's residuals */
+} lpb_lp_status;
+
+typedef enum { LPB_FP64 = 0, LPB_MIXED = 1 } lpb_precision;
+
+typedef struct {
+    int32_t precision;              /* LPB_FP64: FP64 iterates; LPB_MIXED: FP32 iterates and SpMM,
+                                       FP64 residuals, restart tests and scaling factors */
+    int32_t check_every;            /* iterations between residual evaluations (default 64) */
+    int32_t ruiz_iters;             /* Ruiz infinity-norm passes (default 10) */
+    int32_t pock_chambolle;         /* 1: one Pock-Chambolle (alpha = 1) pass after Ruiz */
+    double beta_s, beta_n, beta_a;  /* restart conditions of Sec. 4 (0.2, 0.8, 0.36) */
+    double theta;                   /* primal-weight smoothing (0.5) */
+    double mnorm_sign;              /* sign of the A terms of the M-norm, Eq. residual (-1) */
+    int32_t restart_to_pdhg_output; /* 1: the new anchor is T(z) at the check; 0: the Halpern iterate */
+    int32_t power_max_iter;         /* power iteration for ||A||_2 (5000) */
+    double power_tol;               /* relative change that stops it (1e-10) */
+    uint64_t power_seed;            /* SplitMix64 seed of its start vector */
+    double eps_infeas;              /* infeasibility tolerance; < 0 uses the solve's tol */
+    int32_t detect_infeasibility;   /* 1: evaluate Eq. primal-infeas and dual-infeas */
+    int32_t profile;                /* 1: time every iteration kernel with CUDA events */
+    void* cuda_stream;              /* cudaStream_t to run on, or NULL */
+    int32_t device;                 /* CUDA device ordinal, or -1 for the current device */
+} lpb_options;
+
+/* One override record (Sec. 5.1, 5.2). */
+typedef struct {
+    int32_t kind;  /* 0: base LP; 1: bound change on var; 2: objective sign * e_var */
+    int32_t var;   /* variable index for kinds 1 and 2 */
+    double lo, hi; /* kind 1: the child's box for var is [max(xlo[var], lo), min(xhi[var], hi)];
+                      pass -HUGE_VAL / +HUGE_VAL to keep a side.  lo > hi after that
+                      intersection makes the LP PRIMAL_INFEASIBLE with 0 iterations. */
+    double sign;   /* kind 2: +1 minimises x_var, -1 maximises it (objective -x_var) */
+} lpb_lp_spec;
+
+typedef struct {
+    int32_t status;      /* lpb_lp_status */
+    int32_t restarts;    /* batch restarts taken while this LP was active */
+    int64_t iters;       /* PDHG iterations applied to this LP */
+    double obj;          /* c^T x at the returned point */
+    double dual_obj;     /* -phi_[xlo,xhi](r) - phi_[l,u](y) (Sec. 3) */
+    double rel_primal;   /* ||Ax - Pi_[l,u](Ax)|| / (1 + ||Ax||) */
+    double rel_dual;     /* ||c + A^T y + r|| / (1 + ||c||) */
+    double rel_gap;      /* |c^T x + phi + phi| / (1 + |c^T x| + |phi + phi|) */
+} lpb_lp_result;
+
+/* Per-kernel timing gathered when lpb_options.profile = 1 (CUDA events on the
+ * handle's stream).  bytes = algorithmic bytes: A's values and indices, its
+ * row pointers and every dense operand counted once per launch. */
+typedef struct {
+    int64_t launches[4];  /* 0: A^T Y primal step, 1: A X dual step, 2: FP64 check SpMMs,
+                             3: check reductions + restart */
+    double ms[4];
+    double bytes[4];
+    double setup_ms;      /* lpb_create device work */
+    int64_t checks, compactions;
+    int64_t kernels;      /* every kernel the solve launched */
+} lpb_profile;
+
+/* Fills *opt with the defaults listed above. */
+void lpb_default_options(lpb_options* opt);
+
+/* Builds a handle (Sec. 3 problem data; Sec. 4 step size).  Copies A (CSR,
+ * FP64 values, m x n, nnz < 2^31), c (n), row bounds l, u (m) and variable
+ * bounds xlo, xhi (n) to the device, then on the device: transposes A,
+ * equilibrates it (Ruiz then Pock-Chambolle; A~ = D_r A D_c), estimates
+ * ||A~||_2 by power iteration and fixes eta = 0.998 / ||A~||_2.
+ * Rejects (LPB_ERR_INVALID_ARG): m < 0, n < 1, negative nnz, a non-monotone
+ * row_ptr, a column index outside [0, n), a non-finite value or cost, NaN
+ * bounds, l > u, xlo > xhi, l = +inf or u = -inf.  opt may be NULL. */
+lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                   const double* vals, const double* c, const double* row_lo, const double* row_hi,
+                   const double* var_lo, const double* var_hi, const lpb_options* opt, lpb_handle* out);
+
+/* Solves num_lps LPs (Sec. 5).  specs: num_lps host records.  tol: relative
+ * KKT tolerance of Eq. stopping (> 0).  max_iter >= 1 caps the PDHG
+ * iterations.  warm_x (n x num_lps, LP q at offset q*n) and warm_y (m x
+ * num_lps) are optional warm starts (NULL: x = projection of 0, y = 0).
+ * On LPB_OK *out owns the results until lpb_batch_free. */
+lpb_err lpb_solve(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs, double tol, int64_t max_iter,
+                  const double* warm_x, const double* warm_y, lpb_batch_t* out);
+
+/* As lpb_solve, with specs_dev, warm_x_dev and warm_y_dev in device memory
+ * of the handle's device (layouts as above; warm pointers may be NULL).
+ * The override records are validated on the device: a variable index out
+ * of range returns LPB_ERR_BAD_INDEX. */
+lpb_err lpb_solve_dev(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs_dev, double tol,
+                      int64_t max_iter, const double* warm_x_dev, const double* warm_y_dev,
+                      lpb_batch_t* out);
+
+/* Result of LP lp of a batch: *res, and optionally x (n doubles) and y (m
+ * doubles) in the original, unscaled space (x = D_c x~, y = D_r y~). */
+lpb_err lpb_result(lpb_batch_t b, int32_t lp, lpb_lp_result* res, double* x, double* y);
+
+/* All num_lps results at once (host array of num_lps records). */
+lpb_err lpb_results(lpb_batch_t b, lpb_lp_result* res);
+
+/* Device pointers to the batch's x (n x num_lps) and y (m x num_lps); owned by
+ * the batch. */
+lpb_err lpb_result_device(lpb_batch_t b, const double** x_dev, const double** y_dev);
+
+/* Kernel timing of a batch solved with profile = 1 (zeros otherwise). */
+lpb_err lpb_batch_profile(lpb_batch_t b, lpb_profile* p);
+
+/* Scalars fixed by lpb_create: eta = 0.998/||A~||_2 and the power-iteration
+ * estimate of ||A~||_2 with the number of products it took. */
+lpb_err lpb_handle_info(lpb_handle h, double* eta, double* norm_est, int32_t* power_iters);
+
+/* Scaling factors D_r (m) and D_c (n) of A~ = D_r A D_c, copied to the host. */
+lpb_err lpb_scaling(lpb_handle h, double* d_row, double* d_col);
+
+void lpb_batch_free(lpb_batch_t b);
+void lpb_destroy(lpb_handle h);
+
+/* Message for the last non-OK return on the calling thread ("" if none). */
+const char* lpb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPB_H */

@@ -1,0 +1,795 @@
+// lpb_check.cu -- what runs every check_every iterations, all in FP64:
+//   the fixed-point residual r = ||T(z) - z||_M (Sec. 4, Eq. residual),
+//   relative KKT residuals at T(z) in the original space (Eq. stopping),
+//   infeasibility certificates (Eq. primal-infeas, dual-infeas),
+//   the batch-averaged restart test and primal-weight update (Sec. 4
+//   "Restarts", "Step-size and primal weight"; Sec. 5 "Restarts"),
+//   and, between checks, extraction of finished LPs and compaction of the
+//   batch (Sec. 5 "Stopping criteria and infeasibility detection").
+// Per-LP sums are reduced in a fixed order (per-block partials, then a
+// fixed tree), so a solve is bitwise reproducible.
+#include "lpb_internal.h"
+
+namespace lpb {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { static constexpr int V = 4; };
+template <> struct Vec<double> { static constexpr int V = 2; };
+
+__device__ __forceinline__ void ldg_d(const float* p, double (&r)[4]) {
+    float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = u.x; r[1] = u.y; r[2] = u.z; r[3] = u.w;
+}
+__device__ __forceinline__ void ldg_d(const double* p, double (&r)[2]) {
+    double2 u = __ldg(reinterpret_cast<const double2*>(p));
+    r[0] = u.x; r[1] = u.y;
+}
+__device__ __forceinline__ void st_d(double* p, const double (&r)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
+}
+__device__ __forceinline__ void st_d(double* p, const double (&r)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+}
+
+__device__ __forceinline__ double proj_box(double v, double a, double b) {
+    double t = v < b ? v : b;
+    return t > a ? t : a;
+}
+// barrier cone B_[a,b] (Sec. 3)
+__device__ __forceinline__ double proj_barrier(double v, double a, double b) {
+    const bool li = isinf(a), hi = isinf(b);
+    if (li && hi) return 0.0;
+    if (li) return v > 0.0 ? v : 0.0;
+    if (hi) return v < 0.0 ? v : 0.0;
+    return v;
+}
+// recession cone R_[a,b]; free where both bounds are infinite
+__device__ __forceinline__ double proj_recession(double v, double a, double b) {
+    const bool li = isinf(a), hi = isinf(b);
+    if (li && hi) return v;
+    if (hi) return v > 0.0 ? v : 0.0;
+    if (li) return v < 0.0 ? v : 0.0;
+    return 0.0;
+}
+// one term of phi_[a,b](v) = b v_+ + a v_-, with 0 * inf = 0
+__device__ __forceinline__ double support(double v, double a, double b) {
+    if (v > 0.0) return b * v;
+    if (v < 0.0) return a * v;
+    return 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 SpMM of one sparse matrix against two dense operands at once
+// ---------------------------------------------------------------------------
+template <typename TX>
+struct SpmmArgs {
+    int rows;
+    const int* rp;
+    const int* ci;
+    const double* va;
+    const int* long_rows;
+    int n_long;
+    const TX* s0;
+    const TX* s1;
+    const TX* s2;
+    double* o0;
+    double* o1;
+    double* o2;
+    int ld, ncol;
+};
+
+// NOPS = 2: (s0, s1) -> (o0, o1); NOPS = 3 adds s2 -> o2
+template <typename TX, int G, int NOPS>
+__global__ void __launch_bounds__(kBlock) k_spmm64(const SpmmArgs<TX> a) {
+    constexpr int V = Vec<TX>::V, GPB = kBlock / G, TN = G * V;
+    __shared__ double red[kBlock * V * NOPS];
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int col0 = blockIdx.y * TN + lane * V;
+    const bool active = col0 < a.ncol;
+    const bool is_long = (int)blockIdx.x < a.n_long;
+    int row, slot = 0, nslot = 1;
+    if (is_long) {
+        row = a.long_rows[blockIdx.x];
+        slot = grp;
+        nslot = GPB;
+    } else {
+        row = ((int)blockIdx.x - a.n_long) * GPB + grp;
+        if (row >= a.rows) return;
+        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+    }
+    double acc[NOPS][V];
+#pragma unroll
+    for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[q][v] = 0.0;
+    const TX* src[3] = {a.s0, a.s1, a.s2};
+    if (active) {
+        const int end = a.rp[row + 1];
+        for (int e = a.rp[row] + slot; e < end; e += nslot) {
+            const int c = a.ci[e];
+            const double w = a.va[e];
+#pragma unroll
+            for (int q = 0; q < NOPS; ++q) {
+                double x[V];
+                ldg_d(src[q] + (size_t)c * a.ld + col0, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[q][v] = fma(w, x[v], acc[q][v]);
+            }
+        }
+    }
+    if (is_long) {
+#pragma unroll
+        for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) red[(q * kBlock + threadIdx.x) * V + v] = acc[q][v];
+        __syncthreads();
+        if (grp != 0) return;
+        for (int g = 1; g < GPB; ++g)
+#pragma unroll
+            for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[q][v] += red[(q * kBlock + g * G + lane) * V + v];
+    }
+    if (!active) return;
+    const size_t off = (size_t)row * a.ld + col0;
+    st_d(a.o0 + off, acc[0]);
+    st_d(a.o1 + off, acc[1]);
+    if (NOPS == 3) st_d(a.o2 + off, acc[NOPS - 1]);
+}
+
+template <typename TX, int G, int NOPS>
+cudaError_t spmm_g(const SpmmArgs<TX>& a, cudaStream_t s) {
+    constexpr int V = Vec<TX>::V, GPB = kBlock / G, TN = G * V;
+    dim3 grid(a.n_long + (a.rows + GPB - 1) / GPB, (a.ncol + TN - 1) / TN);
+    k_spmm64<TX, G, NOPS><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename TX, int NOPS>
+cudaError_t spmm64(const Csr& m, const TX* s0, const TX* s1, const TX* s2, double* o0, double* o1, double* o2,
+                   int ld, int ncol, cudaStream_t s) {
+    if (m.rows == 0 || ncol == 0) return cudaSuccess;
+    SpmmArgs<TX> a{m.rows, m.rp, m.ci, m.v64, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
+    constexpr int V = Vec<TX>::V;
+    const int vecs = (ncol + V - 1) / V;
+    if (vecs <= 1) return spmm_g<TX, 1, NOPS>(a, s);
+    if (vecs <= 2) return spmm_g<TX, 2, NOPS>(a, s);
+    if (vecs <= 4) return spmm_g<TX, 4, NOPS>(a, s);
+    if (vecs <= 8) return spmm_g<TX, 8, NOPS>(a, s);
+    if (vecs <= 16) return spmm_g<TX, 16, NOPS>(a, s);
+    return spmm_g<TX, 32, NOPS>(a, s);
+}
+
+// ---------------------------------------------------------------------------
+// per-column partial sums over the rows (block 32 columns x kReduceRows rows)
+// ---------------------------------------------------------------------------
+template <int NS>
+__device__ __forceinline__ void write_partials(double (&s)[NS], double* part, int stat0, int nb, int ld, int j,
+                                               bool ok) {
+    __shared__ double sh[kReduceRows][32];
+    for (int q = 0; q < NS; ++q) {
+        sh[threadIdx.y][threadIdx.x] = s[q];
+        __syncthreads();
+        if (threadIdx.y == 0) {
+            double t = sh[0][threadIdx.x];
+            for (int r = 1; r < kReduceRows; ++r) t += sh[r][threadIdx.x];
+            if (ok) part[((size_t)(stat0 + q) * nb + blockIdx.x) * ld + j] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+struct ReduceArgs {
+    int m, n, ld, ncol, nb_m, nb_n;
+    const double *d_r, *d_c;
+    const double *c, *xl, *xu, *l, *u;
+    ColCheck col;
+    const T *Xh, *DX, *G, *X0, *X, *Yh, *DY, *DYp, *Y0, *Y;
+    const double *P0, *P1, *Q0, *Q1, *Q2;
+    double* part;
+    int restart_to_output;
+};
+
+template <typename T>
+__global__ void k_reduce_rows_m(const ReduceArgs<T> a) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const bool ok = j < a.ncol;
+    double s[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = 0.0;
+    if (ok) {
+        for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.m; i += gridDim.x * kReduceRows) {
+            const size_t off = (size_t)i * a.ld + j;
+            const double dr = a.d_r[i], l = a.l[i], u = a.u[i];
+            const double ax = a.P0[off] / dr;               // A x, x = D_c x~
+            const double pv = ax - proj_box(ax, l, u);
+            s[0] += pv * pv;
+            s[1] += ax * ax;
+            const double yh = (double)a.Yh[off];
+            s[2] += support(dr * yh, l, u);                 // phi_[l,u](y), y = D_r y~
+            const double dy = (double)a.DY[off];
+            s[3] += dy * dy;
+            s[4] += dy * a.P1[off];                         // <dy~, A~ dx~>
+            const double anchor = a.restart_to_output ? yh : (double)a.Y[off];
+            const double dy0 = anchor - (double)a.Y0[off];
+            s[5] += dy0 * dy0;
+            s[6] += support(dr * (double)a.DYp[off], l, u); // phi(Pi_B(D_r dy~))
+            const double adx = a.P1[off] / dr;              // A dx, dx = D_c dx~
+            const double t = adx - proj_recession(adx, l, u);
+            s[7] += t * t;
+        }
+    }
+    write_partials<8>(s, a.part, S_PRES2, a.nb_m, a.ld, j, ok);
+}
+
+template <typename T>
+__global__ void k_reduce_rows_n(const ReduceArgs<T> a) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const bool ok = j < a.ncol;
+    double s[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) s[q] = 0.0;
+    if (ok) {
+        const int kind = a.col.kind[j], var = a.col.var[j];
+        const double olo = a.col.lo[j], ohi = a.col.hi[j], oc = a.col.c[j];
+        for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.n; i += gridDim.x * kReduceRows) {
+            const size_t off = (size_t)i * a.ld + j;
+            const double dc = a.d_c[i];
+            double cj = a.c[i], lo = a.xl[i], hi = a.xu[i];
+            if (kind == 2) cj = var == i ? oc : 0.0;
+            else if (kind == 1 && var == i) { lo = olo; hi = ohi; }
+            const double xh = (double)a.Xh[off];
+            const double x = proj_box(dc * xh, lo, hi);
+            const double aty = a.Q0[off] / dc;              // A^T y
+            const double q = cj + aty;
+            const double r = proj_barrier(-q, lo, hi);      // reduced cost
+            const double d = q + r;
+            s[0] += d * d;
+            s[1] += cj * cj;
+            s[2] += cj * x;
+            s[3] += support(r, lo, hi);
+            const double dx = (double)a.DX[off];
+            s[4] += dx * dx;
+            const double anchor = a.restart_to_output ? xh : (double)a.X[off];
+            const double dx0 = anchor - (double)a.X0[off];
+            s[5] += dx0 * dx0;
+            const double gk = (a.Q0[off] - a.Q2[off]) / dc; // A^T y^k = A^T y^ - A^T (y^ - y^k)
+            const double rk = proj_barrier(-cj - gk, lo, hi);
+            const double drr = proj_barrier(r - rk, lo, hi);
+            s[6] += support(drr, lo, hi);
+            const double t = a.Q1[off] / dc + drr;          // A^T dy + dr
+            s[7] += t * t;
+            const double dxo = dc * dx;
+            s[8] += cj * dxo;
+            const double t2 = dxo - proj_recession(dxo, lo, hi);
+            s[9] += t2 * t2;
+        }
+    }
+    write_partials<10>(s, a.part, S_DRES2, a.nb_n, a.ld, j, ok);
+}
+
+// colsum[s][j] = sum over the blocks' partials, in a fixed order.  The
+// partials of statistic s start at s * kReduceBlocks * ld.
+__global__ void k_colsum(const double* __restrict__ part, int nb_m, int nb_n, int ld, int ncol,
+                         double* __restrict__ colsum) {
+    __shared__ double sh[32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int s = blockIdx.y;
+    const int nb = s < S_DRES2 ? nb_m : nb_n;
+    double acc = 0.0;
+    if (j < ncol) {
+        const double* p = part + (size_t)s * kReduceBlocks * ld;
+        for (int b = threadIdx.y; b < nb; b += 32) acc += p[(size_t)b * ld + j];
+    }
+    sh[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 16; w > 0; w >>= 1) {
+        if ((int)threadIdx.y < w) sh[threadIdx.y][threadIdx.x] += sh[threadIdx.y + w][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && j < ncol) colsum[(size_t)s * ld + j] = sh[0][threadIdx.x];
+}
+
+template <typename T>
+struct DecideArgs {
+    const double* colsum;
+    int ld, ncol;
+    ColCheck col;
+    ColParams<T> colp;
+    double eta, tol, eps_inf, mnorm_sign, beta_s, beta_n, beta_a, theta;
+    int detect_inf, interval_len, final_check;
+    long long k_eval_global;
+    ColRecord* rec;
+    Control* ctl;
+};
+
+constexpr int kDecideThreads = 1024;
+
+// Per-LP status from the summed statistics, then the batch-averaged restart
+// test and, on a restart, the primal-weight update of every LP still active.
+template <typename T>
+__global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a) {
+    __shared__ double sh_sum[kDecideThreads / 32];
+    __shared__ int sh_cnt[kDecideThreads / 32];
+    __shared__ int sh_restart;
+    double lsum = 0.0;
+    int lcnt = 0;
+    const size_t ld = (size_t)a.ld;
+    for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
+        double st[kNumStats];
+        for (int s = 0; s < kNumStats; ++s) st[s] = a.colsum[s * ld + j];
+        const double rel_p = sqrt(st[S_PRES2]) / (1.0 + sqrt(st[S_AX2]));
+        const double rel_d = sqrt(st[S_DRES2]) / (1.0 + sqrt(st[S_C2]));
+        const double dsum = st[S_PHR] + st[S_PHY];
+        const double ctx = st[S_CTX];
+        const double rel_g = isfinite(dsum) ? fabs(ctx + dsum) / (1.0 + fabs(ctx) + fabs(dsum)) : INFINITY;
+        const double w = a.col.w[j];
+        const double r2 = (w / a.eta) * st[S_DX2] + (1.0 / (a.eta * w)) * st[S_DY2] + 2.0 * a.mnorm_sign * st[S_CROSS];
+        const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
+        int status = -1;
+        if (isnan(ctx) || isnan(dsum) || isnan(rel_p) || isnan(rel_d) || isnan(rel_g) || !isfinite(r)) {
+            status = LPB_NUMERICAL;
+        } else if (rel_p <= a.tol && rel_d <= a.tol && rel_g <= a.tol) {
+            status = LPB_OPTIMAL;
+        } else if (a.detect_inf) {
+            const double ph = st[S_PHIDY] + st[S_PHIDR];
+            const double cdx = st[S_CDX];
+            if (ph < 0.0 && sqrt(st[S_RES2]) <= a.eps_inf * fabs(ph)) status = LPB_PRIMAL_INFEASIBLE;
+            else if (cdx < 0.0 && sqrt(st[S_RX2]) <= a.eps_inf * fabs(cdx) &&
+                     sqrt(st[S_RA2]) <= a.eps_inf * fabs(cdx))
+                status = LPB_DUAL_INFEASIBLE;
+        }
+        ColRecord rc;
+        rc.status = status;
+        rc.pad = 0;
+        rc.r = r;
+        rc.obj = ctx;
+        rc.dual_obj = -dsum;
+        rc.rel_primal = rel_p;
+        rc.rel_dual = rel_d;
+        rc.rel_gap = rel_g;
+        a.rec[j] = rc;
+        if (status < 0) {
+            lsum += r;
+            ++lcnt;
+        }
+    }
+    // deterministic block sum
+    for (int o = 16; o > 0; o >>= 1) {
+        lsum += __shfl_down_sync(kFull, lsum, o);
+        lcnt += __shfl_down_sync(kFull, lcnt, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh_sum[warp] = lsum;
+        sh_cnt[warp] = lcnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        int cnt = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            tot += sh_sum[q];
+            cnt += sh_cnt[q];
+        }
+        Control* c = a.ctl;
+        int restart = 0;
+        double rt = cnt > 0 ? tot / cnt : 0.0;
+        if (cnt > 0 && !a.final_check) {
+            if (c->r0 < 0.0) {
+                c->r0 = rt;
+                c->r_prev = rt;
+            }
+            const long long k_eval = (long long)c->k + a.interval_len - 1;
+            restart = (rt <= a.beta_s * c->r0) || (rt <= a.beta_n * c->r0 && rt > c->r_prev) ||
+                      ((double)k_eval > a.beta_a * (double)a.k_eval_global);
+            if (restart) {
+                c->k = 0;
+                c->r0 = rt;
+                c->r_prev = rt;
+                c->restarts += 1;
+            } else {
+                c->k += a.interval_len;
+                c->r_prev = rt;
+            }
+        }
+        c->restart = restart;
+        c->r_avg = rt;
+        sh_restart = restart;
+    }
+    __syncthreads();
+    if (!sh_restart) return;
+    for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
+        if (a.rec[j].status >= 0) continue;
+        const double ddx = a.colsum[S_DX02 * ld + j], ddy = a.colsum[S_DY02 * ld + j];
+        const double d = sqrt(ddy) / sqrt(ddx);   // ||y^{n+1,0} - y^{n,0}|| / ||x^{n+1,0} - x^{n,0}||
+        if (ddx > 0.0 && ddy > 0.0 && isfinite(d) && d > 0.0) {
+            const double w = exp(a.theta * log(d) + (1.0 - a.theta) * log(a.col.w[j]));
+            a.col.w[j] = w;
+            a.colp.tau[j] = (T)(a.eta / w);
+            a.colp.sigma[j] = (T)(a.eta * w);
+        }
+    }
+}
+
+// On a restart: anchor and iterate <- T(z) at the check (or the anchor <-
+// the Halpern iterate for restart_to_output = 0).
+template <typename T>
+__global__ void k_restart_copy(T* __restrict__ Z, T* __restrict__ Z0, const T* __restrict__ Zh, int rows, int ld,
+                               int ncol, int to_output, const Control* __restrict__ ctl) {
+    if (!ctl->restart) return;
+    const size_t total = (size_t)rows * ld;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(p % ld);
+        if (j >= ncol) continue;
+        if (to_output) {
+            const T v = Zh[p];
+            Z[p] = v;
+            Z0[p] = v;
+        } else {
+            Z0[p] = Z[p];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batch set-up, extraction, compaction
+// ---------------------------------------------------------------------------
+template <typename T>
+struct InitArgs {
+    int m, n, ld, ncol;
+    const lpb_lp_spec* specs;
+    const double *d_r, *d_c, *xl, *xu;   // original box
+    const T *xls, *xus;                  // scaled box, iterate precision
+    double eta, c_norm_base, b_norm;
+    ColParams<T> colp;
+    ColCheck colc;
+    ColRecord* rec;
+    Control* ctl;
+};
+
+// runs before k_init_columns, whose blocks may raise ctl->error
+__global__ void k_init_control(Control* ctl) {
+    ctl->k = 0;
+    ctl->restart = 0;
+    ctl->error = 0;
+    ctl->pad = 0;
+    ctl->r0 = -1.0;
+    ctl->r_prev = -1.0;
+    ctl->r_avg = 0.0;
+    ctl->restarts = 0;
+}
+
+template <typename T>
+__global__ void k_init_columns(const InitArgs<T> a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.ld) return;
+    int kind = 0, var = -1;
+    double olo = 0.0, ohi = 0.0, oc = 0.0;
+    T slo = T(0), shi = T(0), sc = T(0);
+    double cn = a.c_norm_base;
+    int status = -1;
+    if (j < a.ncol) {
+        const lpb_lp_spec sp = a.specs[j];
+        kind = sp.kind;
+        var = sp.var;
+        if (kind < 0 || kind > 2) {
+            atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
+            kind = 0;
+        }
+        if (kind != 0 && (var < 0 || var >= a.n)) {
+            atomicMax(&a.ctl->error, (int)LPB_ERR_BAD_INDEX);
+            kind = 0;
+        }
+        if (kind == 0) var = -1;
+        if (kind == 1) {
+            olo = sp.lo > a.xl[var] ? sp.lo : a.xl[var];
+            ohi = sp.hi < a.xu[var] ? sp.hi : a.xu[var];
+            if (isnan(sp.lo) || isnan(sp.hi)) atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
+            if (olo > ohi) status = LPB_PRIMAL_INFEASIBLE;
+            slo = (T)(olo / a.d_c[var]);
+            shi = (T)(ohi / a.d_c[var]);
+        } else if (kind == 2) {
+            if (!isfinite(sp.sign)) atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
+            oc = sp.sign;
+            sc = (T)(a.d_c[var] * sp.sign);
+            cn = fabs(a.d_c[var] * sp.sign);
+        }
+    }
+    double w = 1.0;
+    const double w0 = cn / a.b_norm;
+    if (cn > 0.0 && a.b_norm > 0.0 && isfinite(w0)) w = w0;
+    a.colp.kind[j] = kind;
+    a.colp.var[j] = var;
+    a.colp.lo[j] = slo;
+    a.colp.hi[j] = shi;
+    a.colp.c[j] = sc;
+    a.colp.tau[j] = (T)(a.eta / w);
+    a.colp.sigma[j] = (T)(a.eta * w);
+    a.colc.kind[j] = kind;
+    a.colc.var[j] = var;
+    a.colc.lo[j] = olo;
+    a.colc.hi[j] = ohi;
+    a.colc.c[j] = oc;
+    a.colc.w[j] = w;
+    a.colc.lp[j] = j;
+    if (j < a.ncol) {
+        ColRecord rc;
+        rc.status = status;
+        rc.pad = 0;
+        rc.r = 0.0;
+        rc.obj = rc.dual_obj = rc.rel_primal = rc.rel_dual = rc.rel_gap = NAN;
+        a.rec[j] = rc;
+    }
+}
+
+// z0 = (Pi_box(warm_x / D_c), warm_y / D_r), or (Pi_box(0), 0)
+template <typename T>
+__global__ void k_init_iterates(const InitArgs<T> a, T* X, T* X0, T* Y, T* Y0, const double* warm_x,
+                                const double* warm_y) {
+    const size_t nx = (size_t)a.n * a.ld, ny = (size_t)a.m * a.ld;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < nx + ny; p += (size_t)gridDim.x * blockDim.x) {
+        if (p < nx) {
+            const int i = (int)(p / a.ld), j = (int)(p % a.ld);
+            T v = T(0);
+            if (j < a.ncol) {
+                T lo = a.xls[i], hi = a.xus[i];
+                const int kind = a.colp.kind[j];
+                if (kind == 1 && a.colp.var[j] == i) { lo = a.colp.lo[j]; hi = a.colp.hi[j]; }
+                const T w = warm_x ? (T)(warm_x[(size_t)j * a.n + i] / a.d_c[i]) : T(0);
+                T t = w < hi ? w : hi;
+                v = t > lo ? t : lo;
+            }
+            X[p] = v;
+            X0[p] = v;
+        } else {
+            const size_t q = p - nx;
+            const int i = (int)(q / a.ld), j = (int)(q % a.ld);
+            T v = T(0);
+            if (j < a.ncol && warm_y) v = (T)(warm_y[(size_t)j * a.m + i] / a.d_r[i]);
+            Y[q] = v;
+            Y0[q] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_extract(int n, int m, int ld, const int* __restrict__ cols, const int* __restrict__ lps, int count,
+                          const double* __restrict__ d_r, const double* __restrict__ d_c, const double* __restrict__ xl,
+                          const double* __restrict__ xu, ColCheck colc, const T* __restrict__ Xh,
+                          const T* __restrict__ Yh, double* __restrict__ x_out, double* __restrict__ y_out) {
+    const int f = blockIdx.y;
+    if (f >= count) return;
+    const int j = cols[f], lp = lps[f];
+    const int kind = colc.kind[j], var = colc.var[j];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n > m ? n : m); i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            double lo = xl[i], hi = xu[i];
+            if (kind == 1 && var == i) { lo = colc.lo[j]; hi = colc.hi[j]; }
+            x_out[(size_t)lp * n + i] = proj_box(d_c[i] * (double)Xh[(size_t)i * ld + j], lo, hi);
+        }
+        if (i < m) y_out[(size_t)lp * m + i] = d_r[i] * (double)Yh[(size_t)i * ld + j];
+    }
+}
+
+// moves column src[p] -> dst[p] in every row of the state blocks
+template <typename T>
+__global__ void k_compact_rows(T* X, T* X0, T* Y, T* Y0, int n, int m, int ld, const int* __restrict__ src,
+                               const int* __restrict__ dst, int count) {
+    const size_t total = (size_t)(n + m) * count;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int mv = (int)(p % count);
+        const int row = (int)(p / count);
+        const int s = src[mv], d = dst[mv];
+        if (row < n) {
+            const size_t r = (size_t)row * ld;
+            X[r + d] = X[r + s];
+            X0[r + d] = X0[r + s];
+        } else {
+            const size_t r = (size_t)(row - n) * ld;
+            Y[r + d] = Y[r + s];
+            Y0[r + d] = Y0[r + s];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_compact_cols(ColParams<T> cp, ColCheck cc, const int* __restrict__ src, const int* __restrict__ dst,
+                               int count) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count) return;
+    const int s = src[p], d = dst[p];
+    cp.kind[d] = cp.kind[s];
+    cp.var[d] = cp.var[s];
+    cp.lo[d] = cp.lo[s];
+    cp.hi[d] = cp.hi[s];
+    cp.c[d] = cp.c[s];
+    cp.tau[d] = cp.tau[s];
+    cp.sigma[d] = cp.sigma[s];
+    cc.kind[d] = cc.kind[s];
+    cc.var[d] = cc.var[s];
+    cc.lo[d] = cc.lo[s];
+    cc.hi[d] = cc.hi[s];
+    cc.c[d] = cc.c[s];
+    cc.w[d] = cc.w[s];
+    cc.lp[d] = cc.lp[s];
+}
+
+inline int blocks_for(size_t work, int threads, int cap = 8192) {
+    size_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int64_t k_eval_global,
+                         int interval_len, bool final_check, double* P, double* Q, double* partials, double* colsum,
+                         ColRecord* rec, Control* ctl, ColParams<T> colp, cudaStream_t s, cudaEvent_t* ev) {
+    cudaError_t e;
+    const int m = d.m, n = d.n;
+    double* P0 = P;
+    double* P1 = P + (size_t)(m > 0 ? m : 1) * ld;
+    double* Q0 = Q;
+    double* Q1 = Q + (size_t)n * ld;
+    double* Q2 = Q + 2 * (size_t)n * ld;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    // A~ [x^, x^ - x] and A~^T [y^, Pi_B(y^ - y), y^ - y] in FP64
+    if ((e = spmm64<T, 2>(d.A, b.Xh, b.DX, nullptr, P0, P1, nullptr, ld, ncol, s)) != cudaSuccess) return e;
+    if ((e = spmm64<T, 3>(d.At, b.Yh, b.DYp, b.DY, Q0, Q1, Q2, ld, ncol, s)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+
+    const int tiles = (ncol + 31) / 32;
+    const int nb_m = m > 0 ? (int)((m + kReduceRows - 1) / kReduceRows < kReduceBlocks ? (m + kReduceRows - 1) / kReduceRows : kReduceBlocks) : 0;
+    const int nb_n = (int)((n + kReduceRows - 1) / kReduceRows < kReduceBlocks ? (n + kReduceRows - 1) / kReduceRows : kReduceBlocks);
+    ReduceArgs<T> ra{};
+    ra.m = m;
+    ra.n = n;
+    ra.ld = ld;
+    ra.ncol = ncol;
+    ra.nb_m = kReduceBlocks;  // partial layout stride: statistic s starts at s * kReduceBlocks * ld
+    ra.nb_n = kReduceBlocks;
+    ra.d_r = d.d_r;
+    ra.d_c = d.d_c;
+    ra.c = d.c;
+    ra.xl = d.xl;
+    ra.xu = d.xu;
+    ra.l = d.l;
+    ra.u = d.u;
+    ra.col = d.col;
+    ra.Xh = b.Xh;
+    ra.DX = b.DX;
+    ra.G = b.G;
+    ra.X0 = b.X0;
+    ra.X = b.X;
+    ra.Yh = b.Yh;
+    ra.DY = b.DY;
+    ra.DYp = b.DYp;
+    ra.Y0 = b.Y0;
+    ra.Y = b.Y;
+    ra.P0 = P0;
+    ra.P1 = P1;
+    ra.Q0 = Q0;
+    ra.Q1 = Q1;
+    ra.Q2 = Q2;
+    ra.part = partials;
+    ra.restart_to_output = d.restart_to_output;
+    const dim3 rblock(32, kReduceRows);
+    if (nb_m > 0) {
+        k_reduce_rows_m<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(ra);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_reduce_rows_n<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(ra);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_colsum<<<dim3(tiles, kNumStats), dim3(32, 32), 0, s>>>(partials, nb_m, nb_n, ld, ncol, colsum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    DecideArgs<T> da{};
+    da.colsum = colsum;
+    da.ld = ld;
+    da.ncol = ncol;
+    da.col = d.col;
+    da.colp = colp;
+    da.eta = d.eta;
+    da.tol = d.tol;
+    da.eps_inf = d.eps_inf;
+    da.mnorm_sign = d.mnorm_sign;
+    da.beta_s = d.beta_s;
+    da.beta_n = d.beta_n;
+    da.beta_a = d.beta_a;
+    da.theta = d.theta;
+    da.detect_inf = d.detect_inf;
+    da.interval_len = interval_len;
+    da.final_check = final_check ? 1 : 0;
+    da.k_eval_global = (long long)k_eval_global;
+    da.rec = rec;
+    da.ctl = ctl;
+    k_decide<T><<<1, kDecideThreads, 0, s>>>(da);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_restart_copy<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.X0, b.Xh, n, ld, ncol,
+                                                                      d.restart_to_output, ctl);
+    if (m > 0)
+        k_restart_copy<T><<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(b.Y, b.Y0, b.Yh, m, ld, ncol,
+                                                                          d.restart_to_output, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int ncol,
+                        const lpb_lp_spec* specs_dev, const double* warm_x, const double* warm_y, double c_norm_base,
+                        double b_norm, ColRecord* rec, Control* ctl, cudaStream_t s) {
+    InitArgs<T> a{};
+    a.m = d.m;
+    a.n = d.n;
+    a.ld = ld;
+    a.ncol = ncol;
+    a.specs = specs_dev;
+    a.d_r = d.d_r;
+    a.d_c = d.d_c;
+    a.xl = d.xl;
+    a.xu = d.xu;
+    a.xls = it.xl;
+    a.xus = it.xu;
+    a.eta = d.eta;
+    a.c_norm_base = c_norm_base;
+    a.b_norm = b_norm;
+    a.colp = it.col;
+    a.colc = d.col;
+    a.rec = rec;
+    a.ctl = ctl;
+    k_init_control<<<1, 1, 0, s>>>(ctl);
+    k_init_columns<T><<<(ld + 255) / 256, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_init_iterates<T><<<blocks_for((size_t)(d.n + d.m) * ld, 256), 256, 0, s>>>(a, b.X, b.X0, b.Y, b.Y0, warm_x,
+                                                                                 warm_y);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev, const int* lps_dev,
+                           int count, const double* xl_base, const double* xu_base, double* x_out, double* y_out,
+                           cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int rows = d.n > d.m ? d.n : d.m;
+    dim3 grid(blocks_for(rows, 256, 1024), count);
+    k_extract<T><<<grid, 256, 0, s>>>(d.n, d.m, ld, cols_dev, lps_dev, count, d.d_r, d.d_c, xl_base, xu_base, d.col,
+                                      b.Xh, b.Yh, x_out, y_out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int* src_dev, const int* dst_dev,
+                           int count, ColParams<T> colp, ColCheck colc, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_compact_rows<T><<<blocks_for((size_t)(n + m) * count, 256), 256, 0, s>>>(b.X, b.X0, b.Y, b.Y0, n, m, ld,
+                                                                                src_dev, dst_dev, count);
+    k_compact_cols<T><<<(count + 255) / 256, 256, 0, s>>>(colp, colc, src_dev, dst_dev, count);
+    return cudaGetLastError();
+}
+
+#define LPB_INSTANTIATE(T)                                                                                           \
+    template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int64_t, int, bool, double*, \
+                                         double*, double*, double*, ColRecord*, Control*, ColParams<T>, cudaStream_t, \
+                                         cudaEvent_t*);                                                               \
+    template cudaError_t launch_init<T>(const CheckData&, const IterData<T>&, const IterBufs<T>&, int, int,           \
+                                        const lpb_lp_spec*, const double*, const double*, double, double,             \
+                                        ColRecord*, Control*, cudaStream_t);                                          \
+    template cudaError_t launch_extract<T>(const CheckData&, const IterBufs<T>&, int, const int*, const int*, int,    \
+                                           const double*, const double*, double*, double*, cudaStream_t);             \
+    template cudaError_t launch_compact<T>(const IterBufs<T>&, int, int, int, const int*, const int*, int,            \
+                                           ColParams<T>, ColCheck, cudaStream_t);
+LPB_INSTANTIATE(float)
+LPB_INSTANTIATE(double)
+
+}  // namespace lpb

@@ -1,0 +1,186 @@
+// lpb_internal.h -- device data layout and kernel launchers shared by the
+// library's translation units (setup, iteration, check, C ABI).
+//
+// Layout in HBM (one handle):
+//   A~ and A~^T as CSR with int32 row pointers and column indices; values in
+//   FP64 (checks, FP64 path) and, for the mixed path, FP32.
+//   Iterate blocks are row-major with the batch contiguous: element (i, j) of
+//   an n x N block lives at i * ld + j, ld = capacity rounded up to 4, so a
+//   row of the batch is one contiguous, 16-byte aligned vector that a CSR
+//   gather reads with 128-bit loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lpb.h"
+
+namespace lpb {
+
+constexpr int kBlock = 256;        // threads of every iteration / SpMM block
+constexpr int kLongRow = 128;      // rows with more nonzeros get a whole block
+constexpr int kReduceRows = 8;     // rows per step of a reduction block (blockDim.y)
+constexpr int kReduceBlocks = 304; // reduction blocks per column tile (2 per SM)
+constexpr int kNumStats = 18;      // per-column partial sums of a check
+
+// per-column statistics produced by a check (indices into the stats arrays)
+enum Stat {
+    // from the m rows
+    S_PRES2 = 0,  // ||Ax - Pi(Ax)||^2 (original space)
+    S_AX2,        // ||Ax||^2
+    S_PHY,        // phi_[l,u](y)
+    S_DY2,        // ||y^ - y||^2 (scaled)
+    S_CROSS,      // <y^ - y, A~ (x^ - x)> (scaled)
+    S_DY02,       // ||y^ - y0||^2 (scaled)
+    S_PHIDY,      // phi_[l,u](dy), dy = Pi_B(D_r (y^ - y))
+    S_RA2,        // ||A dx - Pi_R(A dx)||^2
+    // from the n rows
+    S_DRES2,      // ||c + A^T y + r||^2
+    S_C2,         // ||c||^2
+    S_CTX,        // c^T x
+    S_PHR,        // phi_[xlo,xhi](r)
+    S_DX2,        // ||x^ - x||^2 (scaled)
+    S_DX02,       // ||x^ - x0||^2 (scaled)
+    S_PHIDR,      // phi_[xlo,xhi](dr)
+    S_RES2,       // ||A^T dy + dr||^2
+    S_CDX,        // c^T dx
+    S_RX2         // ||dx - Pi_R(dx)||^2
+};
+
+struct Csr {
+    int rows = 0, cols = 0, nnz = 0;
+    int* rp = nullptr;          // rows + 1
+    int* ci = nullptr;          // nnz
+    double* v64 = nullptr;      // scaled values, FP64
+    float* v32 = nullptr;       // scaled values, FP32 (mixed path)
+    int* long_rows = nullptr;   // rows with > kLongRow entries
+    int n_long = 0;
+};
+
+// Per-column parameters of the iteration kernels (structure of arrays,
+// length >= ld, in the iterate precision T).
+template <typename T>
+struct ColParams {
+    int* kind;   // override kind
+    int* var;    // override variable (or -1)
+    T* lo;       // kind 1: scaled box of var (intersected with the base box)
+    T* hi;
+    T* c;        // kind 2: scaled objective coefficient of var
+    T* tau;      // primal step eta / w
+    T* sigma;    // dual step eta * w
+};
+
+// Per-column data for the FP64 checks, original units.
+struct ColCheck {
+    int* kind;
+    int* var;
+    double* lo;   // kind 1: original box of var (intersected)
+    double* hi;
+    double* c;    // kind 2: sign
+    double* w;    // primal weight
+    int* lp;      // LP index of the column in the caller's batch
+};
+
+// One column's outcome of a check, copied to the host.
+struct ColRecord {
+    int status;   // -1 still active, else lpb_lp_status
+    int pad;
+    double r;     // fixed-point residual (scaled, M-norm)
+    double obj, dual_obj, rel_primal, rel_dual, rel_gap;
+};
+
+// Batch state that lives on the device between checks.
+struct Control {
+    int k;          // inner index of the first iteration of the next interval
+    int restart;    // 1 if the last check restarted
+    int error;      // device-side check flags (LPB_ERR_*)
+    int pad;
+    double r0;      // residual at the start of the epoch (< 0: unset)
+    double r_prev;  // residual at the previous check
+    double r_avg;   // averaged residual of the last check
+    int64_t restarts;
+};
+
+// ---------------------------------------------------------------------------
+// setup (lpb_setup.cu)
+// ---------------------------------------------------------------------------
+cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm_out, cudaStream_t s);
+cudaError_t exclusive_scan_i32(const int* in, int* out, int count, int* total_dev, cudaStream_t s);
+cudaError_t build_long_rows(Csr& a, cudaStream_t s);
+cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& at, const double* at_vals,
+                                int ruiz_iters, int pock_chambolle, double* d_r, double* d_c,
+                                double* tmp_r, double* tmp_c, cudaStream_t s);
+cudaError_t scale_values(const Csr& a, const double* a_vals, const double* d_r, const double* d_c,
+                         bool rows_are_constraints, double* out64, float* out32, cudaStream_t s);
+cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed,
+                       double* work, double* est_out, int* iters_out, cudaStream_t s);
+cudaError_t scale_vectors(int m, int n, const double* d_r, const double* d_c, const double* c,
+                          const double* l, const double* u, const double* xl, const double* xu,
+                          double* cs, double* ls, double* us, double* xls, double* xus, cudaStream_t s);
+cudaError_t sq_norm(const double* v, int count, double* out_dev, cudaStream_t s);
+cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev, cudaStream_t s);
+cudaError_t convert_f32(const double* in, float* out, int count, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// iteration (lpb_iter.cu)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct IterBufs {
+    T *X, *X0, *Xbar, *Y, *Y0;         // state
+    T *Xh, *DX, *G, *Yh, *DY, *DYp;    // written on check iterations
+};
+
+template <typename T>
+struct IterData {
+    Csr A, At;                 // scaled CSRs (values in T taken from v64 / v32)
+    const T* a_vals;
+    const T* at_vals;
+    const T *c, *xl, *xu;      // scaled base vectors (n)
+    const T *l, *u;            // scaled row bounds (m)
+    ColParams<T> col;
+};
+
+// One reflected-Halpern PDHG iteration on columns [0, ncol): primal step
+// (A~^T Y fused with the box projection, reflection and Halpern update) then
+// dual step (A~ Xbar fused with the row projection and Halpern update).
+// k_dev[0] + t is the inner index k of Eq. mainiter.
+template <typename T>
+cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol,
+                             const int* k_dev, int t, bool check, cudaStream_t s,
+                             cudaEvent_t* ev /* 3 events or nullptr */);
+
+// ---------------------------------------------------------------------------
+// checks (lpb_check.cu)
+// ---------------------------------------------------------------------------
+struct CheckData {
+    Csr A, At;                     // FP64 values in v64
+    int m, n;
+    const double *d_r, *d_c;
+    const double *c, *xl, *xu;     // original base vectors (n)
+    const double *l, *u;           // original row bounds (m)
+    ColCheck col;
+    double eta, beta_s, beta_n, beta_a, theta, mnorm_sign, eps_inf, tol;
+    int detect_inf, restart_to_output;
+};
+
+template <typename T>
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int64_t k_eval_global,
+                         int interval_len, bool final_check, double* P, double* Q, double* partials,
+                         double* colsum, ColRecord* rec, Control* ctl, ColParams<T> colp, cudaStream_t s,
+                         cudaEvent_t* ev /* 3 events or nullptr */);
+
+template <typename T>
+cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int ncol,
+                        const lpb_lp_spec* specs_dev, const double* warm_x, const double* warm_y,
+                        double c_norm_base, double b_norm, ColRecord* rec, Control* ctl, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev,
+                           const int* lps_dev, int count, const double* xl_base, const double* xu_base,
+                           double* x_out, double* y_out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int* src_dev, const int* dst_dev,
+                           int count, ColParams<T> colp, ColCheck colc, cudaStream_t s);
+
+}  // namespace lpb

@@ -1,0 +1,590 @@
+// lpb_setup.cu -- once-per-matrix device work of lpb_create:
+//   transpose of A (A and A^T are both stored, Sec. 6 "Implementation details"),
+//   Ruiz + Pock-Chambolle equilibration, scaled values and vectors,
+//   power iteration for ||A~||_2 (eta = 0.998 / ||A~||_2, Sec. 4 "Step-size"),
+//   lists of long rows for the SpMM kernels.
+// Every kernel is deterministic: sums run in a fixed order, the transpose is
+// sorted by the original entry index inside each row of A^T.
+#include <climits>
+#include <cstdio>
+#include <vector>
+
+#include "lpb_internal.h"
+
+namespace lpb {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (block = 1024 threads, 2 elements per thread)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanTile = 2 * kScanThreads;
+
+__global__ void k_scan_tile(const int* __restrict__ in, int* __restrict__ out, int count,
+                            int* __restrict__ tile_sums) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile + 2 * threadIdx.x;
+    int a0 = base < count ? in[base] : 0;
+    int a1 = base + 1 < count ? in[base + 1] : 0;
+    int local = a0 + a1;
+    // inclusive warp scan of `local`
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += t;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    int excl = inc - local + warp_tot[warp];
+    if (base < count) out[base] = excl;
+    if (base + 1 < count) out[base + 1] = excl + a0;
+    if (threadIdx.x == kScanThreads - 1 && tile_sums) tile_sums[blockIdx.x] = excl + local;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int count, const int* __restrict__ tile_offs) {
+    const int base = blockIdx.x * kScanTile + 2 * threadIdx.x;
+    const int add = tile_offs[blockIdx.x];
+    if (base < count) out[base] += add;
+    if (base + 1 < count) out[base + 1] += add;
+}
+
+__global__ void k_copy_total(const int* in_last, const int* out_last, int* total) {
+    *total = *in_last + *out_last;
+}
+
+// ---------------------------------------------------------------------------
+// transpose
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(const int* __restrict__ ci, int nnz, int* __restrict__ cnt) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[e]], 1);
+}
+
+// one warp per row of A: every entry takes a slot in its column's segment
+__global__ void k_fill_slots(const int* __restrict__ rp, const int* __restrict__ ci, int rows,
+                             const int* __restrict__ rp_t, int* __restrict__ cursor, int* __restrict__ key) {
+    const int warps = gridDim.x * blockDim.x / 32;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < rows; i += warps) {
+        for (int e = rp[i] + (threadIdx.x & 31); e < rp[i + 1]; e += 32) {
+            int j = ci[e];
+            int pos = rp_t[j] + atomicAdd(&cursor[j], 1);
+            key[pos] = e;
+        }
+    }
+}
+
+// segments of <= 32 keys: one warp, bitonic network in registers
+__global__ void k_segsort_warp(const int* __restrict__ seg, int nseg, int* __restrict__ key) {
+    const int warps = gridDim.x * blockDim.x / 32;
+    const int lane = threadIdx.x & 31;
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) / 32; s < nseg; s += warps) {
+        const int beg = seg[s], len = seg[s + 1] - beg;
+        if (len <= 1 || len > 32) continue;
+        int v = lane < len ? key[beg + lane] : INT_MAX;
+        for (int k = 2; k <= 32; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                int o = __shfl_xor_sync(kFull, v, j);
+                bool asc = (lane & k) == 0, lower = (lane & j) == 0;
+                v = (asc == lower) ? min(v, o) : max(v, o);
+            }
+        if (lane < len) key[beg + lane] = v;
+    }
+}
+
+// segments of 33..2048 keys: one block, bitonic network in shared memory
+constexpr int kSegBlock = 2048;
+__global__ void k_segsort_block(const int* __restrict__ seg, int nseg, int* __restrict__ key) {
+    __shared__ int buf[kSegBlock];
+    for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const int beg = seg[s], len = seg[s + 1] - beg;
+        if (len <= 32 || len > kSegBlock) continue;
+        int p = 64;
+        while (p < len) p <<= 1;
+        for (int i = threadIdx.x; i < p; i += blockDim.x) buf[i] = i < len ? key[beg + i] : INT_MAX;
+        __syncthreads();
+        for (int k = 2; k <= p; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                    int q = i ^ j;
+                    if (q > i) {
+                        bool asc = (i & k) == 0;
+                        int a = buf[i], b = buf[q];
+                        if ((a > b) == asc) { buf[i] = b; buf[q] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) key[beg + i] = buf[i];
+        __syncthreads();
+    }
+}
+
+__device__ int lower_bound_i(const int* a, int n, int v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// segments of > 2048 keys: one block, bottom-up merge sort through `tmp`
+// (keys are distinct entry indices, so a key's rank in the other run fixes
+// its output position)
+__global__ void k_segsort_big(const int* __restrict__ seg, int nseg, int* __restrict__ key, int* __restrict__ tmp) {
+    for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const int beg = seg[s], len = seg[s + 1] - beg;
+        if (len <= kSegBlock) continue;
+        int* src = key + beg;
+        int* dst = tmp + beg;
+        for (int w = 1; w < len; w <<= 1) {
+            for (int p = threadIdx.x; p < len; p += blockDim.x) {
+                int lo = (p / (2 * w)) * (2 * w);
+                int mid = min(lo + w, len), hi = min(lo + 2 * w, len);
+                int v = src[p];
+                int pos = p < mid ? (p - lo) + lower_bound_i(src + mid, hi - mid, v)
+                                  : (p - mid) + lower_bound_i(src + lo, mid - lo, v);
+                dst[lo + pos] = v;
+            }
+            __syncthreads();
+            int* t = src; src = dst; dst = t;
+        }
+        if (src != key + beg)
+            for (int p = threadIdx.x; p < len; p += blockDim.x) key[beg + p] = src[p];
+        __syncthreads();
+    }
+}
+
+// A^T entry at `pos` comes from A entry key[pos]: its column in A^T is the
+// row of that entry in A (binary search in row_ptr), its value is A's value.
+__global__ void k_finish_transpose(const int* __restrict__ rp, int rows, const int* __restrict__ key, int nnz,
+                                   const double* __restrict__ vals, int* __restrict__ ci_t,
+                                   double* __restrict__ vals_t) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += gridDim.x * blockDim.x) {
+        int e = key[p];
+        int lo = 0, hi = rows;  // last row with rp[row] <= e
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (rp[mid] <= e) lo = mid; else hi = mid;
+        }
+        ci_t[p] = lo;
+        vals_t[p] = vals[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// long-row lists
+// ---------------------------------------------------------------------------
+__global__ void k_long_flags(const int* __restrict__ rp, int rows, int* __restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
+        flag[i] = (rp[i + 1] - rp[i]) > kLongRow ? 1 : 0;
+}
+
+__global__ void k_long_scatter(const int* __restrict__ flag, const int* __restrict__ pos, int rows,
+                               int* __restrict__ list) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
+        if (flag[i]) list[pos[i]] = i;
+}
+
+// ---------------------------------------------------------------------------
+// equilibration
+// ---------------------------------------------------------------------------
+// One warp per CSR row: max or sum of |D_r[i] * a * D_c[j]| where, for the
+// CSR of A^T, the row is a variable j and the column a constraint i (the
+// product is always formed in the order D_r * a * D_c).
+template <bool SUM>
+__global__ void k_row_stat(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                           int rows, const double* __restrict__ d_row, const double* __restrict__ d_col,
+                           bool rows_are_constraints, double* __restrict__ out) {
+    const int warps = gridDim.x * blockDim.x / 32;
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < rows; i += warps) {
+        double acc = 0.0;
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+            int j = ci[e];
+            double a = rows_are_constraints ? fabs(d_row[i] * v[e] * d_col[j]) : fabs(d_col[j] * v[e] * d_row[i]);
+            acc = SUM ? acc + a : fmax(acc, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double t = __shfl_down_sync(kFull, acc, o);
+            acc = SUM ? acc + t : fmax(acc, t);
+        }
+        if (lane == 0) out[i] = acc;
+    }
+}
+
+__global__ void k_apply_scale(double* __restrict__ d, const double* __restrict__ stat, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        if (stat[i] > 0.0) d[i] /= sqrt(stat[i]);
+}
+
+__global__ void k_fill_d(double* d, int count, double v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) d[i] = v;
+}
+
+// scaled values: warp per row, D_r[i] * a * D_c[j] with i the constraint
+__global__ void k_scale_vals(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                             int rows, const double* __restrict__ d_r, const double* __restrict__ d_c,
+                             bool rows_are_constraints, double* __restrict__ o64, float* __restrict__ o32) {
+    const int warps = gridDim.x * blockDim.x / 32;
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < rows; i += warps) {
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+            int j = ci[e];
+            double s = rows_are_constraints ? d_r[i] * v[e] * d_c[j] : d_r[j] * v[e] * d_c[i];
+            o64[e] = s;
+            if (o32) o32[e] = (float)s;
+        }
+    }
+}
+
+__global__ void k_scale_vectors(int m, int n, const double* __restrict__ d_r, const double* __restrict__ d_c,
+                                const double* __restrict__ c, const double* __restrict__ l,
+                                const double* __restrict__ u, const double* __restrict__ xl,
+                                const double* __restrict__ xu, double* cs, double* ls, double* us, double* xls,
+                                double* xus) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(m, n); i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            cs[i] = d_c[i] * c[i];
+            xls[i] = xl[i] / d_c[i];
+            xus[i] = xu[i] / d_c[i];
+        }
+        if (i < m) {
+            ls[i] = d_r[i] * l[i];
+            us[i] = d_r[i] * u[i];
+        }
+    }
+}
+
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) out[i] = (float)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// deterministic two-stage sums
+// ---------------------------------------------------------------------------
+constexpr int kSumBlocks = 256;
+constexpr int kSumThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// mode 0: sum v^2; mode 1: sum over rows of b~_i^2 (finite bound of larger magnitude)
+__global__ void k_sum_stage1(const double* __restrict__ a, const double* __restrict__ b, int count, int mode,
+                             double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        if (mode == 0) {
+            acc += a[i] * a[i];
+        } else {
+            double l = a[i], u = b[i], r = 0.0;
+            bool fl = isfinite(l), fu = isfinite(u);
+            if (fl && fu) r = fabs(l) > fabs(u) ? l : u;
+            else if (fl) r = l;
+            else if (fu) r = u;
+            acc += r * r;
+        }
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_sum_stage2(const double* __restrict__ part, int count, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+// ---------------------------------------------------------------------------
+// power iteration
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the index-th output of the
+// generator whose state starts at `seed`.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t index) {
+    uint64_t z = seed + (index + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_power_init(double* v, int n, uint64_t seed) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        v[j] = 2.0 * ((double)(splitmix64(seed, (uint64_t)j) >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// y = M x, warp per row, FP64
+__global__ void k_spmv64(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                         int rows, const double* __restrict__ x, double* __restrict__ y) {
+    const int warps = gridDim.x * blockDim.x / 32;
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < rows; i += warps) {
+        double acc = 0.0;
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) acc += v[e] * x[ci[e]];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+        if (lane == 0) y[i] = acc;
+    }
+}
+
+// v = w / sqrt(*nw2) when the norm is positive; records sqrt(nw2) and
+// sqrt(est2) in the history at `it`
+__global__ void k_power_normalize(double* __restrict__ v, const double* __restrict__ w, int n,
+                                  const double* __restrict__ est2, const double* __restrict__ nw2,
+                                  double* __restrict__ hist_est, double* __restrict__ hist_nw, int it) {
+    double nw = sqrt(*nw2);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        hist_est[it] = sqrt(*est2);
+        hist_nw[it] = nw;
+    }
+    if (!(nw > 0.0)) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) v[j] = w[j] / nw;
+}
+
+inline int grid_for(long long work, int threads, int cap = 4096) {
+    long long g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+cudaError_t exclusive_scan_i32(const int* in, int* out, int count, int* total_dev, cudaStream_t s) {
+    if (count <= 0) {
+        if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(int), s);
+        return cudaSuccess;
+    }
+    const int tiles = (count + kScanTile - 1) / kScanTile;
+    int* sums = nullptr;
+    int* offs = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (tiles > 1) {
+        if ((e = cudaMallocAsync((void**)&sums, sizeof(int) * tiles * 2, s)) != cudaSuccess) return e;
+        offs = sums + tiles;
+    }
+    k_scan_tile<<<tiles, kScanThreads, 0, s>>>(in, out, count, sums);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (tiles > 1) {
+        if ((e = exclusive_scan_i32(sums, offs, tiles, nullptr, s)) != cudaSuccess) return e;
+        k_scan_add<<<tiles, kScanThreads, 0, s>>>(out, count, offs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (total_dev) {
+        k_copy_total<<<1, 1, 0, s>>>(in + count - 1, out + count - 1, total_dev);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (sums) e = cudaFreeAsync(sums, s);
+    return e;
+}
+
+cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm_out, cudaStream_t s) {
+    // at.rp (cols + 1), at.ci (nnz) and perm_out-sized scratch are allocated by the caller;
+    // perm_out receives the A^T slot -> A entry map, vals_t is written into at.v64.
+    cudaError_t e;
+    const int nnz = a.nnz, cols = a.cols;
+    int *cnt = nullptr, *cursor = nullptr, *tmp = nullptr;
+    if ((e = cudaMallocAsync((void**)&cnt, sizeof(int) * (size_t)(cols + 1) * 2, s)) != cudaSuccess) return e;
+    cursor = cnt + cols + 1;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(cols + 1) * 2, s)) != cudaSuccess) return e;
+    if (nnz > 0) {
+        k_count_cols<<<grid_for(nnz, 256), 256, 0, s>>>(a.ci, nnz, cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = exclusive_scan_i32(cnt, at.rp, cols + 1, nullptr, s)) != cudaSuccess) return e;
+    if (nnz > 0) {
+        k_fill_slots<<<grid_for((long long)a.rows * 32, 256), 256, 0, s>>>(a.rp, a.ci, a.rows, at.rp, cursor, perm_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_segsort_warp<<<grid_for((long long)cols * 32, 256), 256, 0, s>>>(at.rp, cols, perm_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_segsort_block<<<grid_for(cols, 1, 1024), 1024, 0, s>>>(at.rp, cols, perm_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void**)&tmp, sizeof(int) * (size_t)nnz, s)) != cudaSuccess) return e;
+        k_segsort_big<<<grid_for(cols, 1, 256), 1024, 0, s>>>(at.rp, cols, perm_out, tmp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_finish_transpose<<<grid_for(nnz, 256), 256, 0, s>>>(a.rp, a.rows, perm_out, nnz, a_vals, at.ci, at.v64);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaFreeAsync(tmp, s)) != cudaSuccess) return e;
+    }
+    return cudaFreeAsync(cnt, s);
+}
+
+cudaError_t build_long_rows(Csr& a, cudaStream_t s) {
+    cudaError_t e;
+    a.n_long = 0;
+    if (a.rows == 0) return cudaSuccess;
+    int *flag = nullptr, *total = nullptr;
+    if ((e = cudaMallocAsync((void**)&flag, sizeof(int) * ((size_t)a.rows * 2 + 1), s)) != cudaSuccess) return e;
+    int* pos = flag + a.rows;
+    total = pos + a.rows;
+    k_long_flags<<<grid_for(a.rows, 256), 256, 0, s>>>(a.rp, a.rows, flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan_i32(flag, pos, a.rows, total, s)) != cudaSuccess) return e;
+    int h_total = 0;
+    if ((e = cudaMemcpyAsync(&h_total, total, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    a.n_long = h_total;
+    if (h_total > 0) {
+        if ((e = cudaMalloc((void**)&a.long_rows, sizeof(int) * (size_t)h_total)) != cudaSuccess) return e;
+        k_long_scatter<<<grid_for(a.rows, 256), 256, 0, s>>>(flag, pos, a.rows, a.long_rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaFreeAsync(flag, s);
+}
+
+cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& at, const double* at_vals,
+                                int ruiz_iters, int pock_chambolle, double* d_r, double* d_c, double* tmp_r,
+                                double* tmp_c, cudaStream_t s) {
+    cudaError_t e;
+    const int m = a.rows, n = a.cols;
+    if (m > 0) k_fill_d<<<grid_for(m, 256), 256, 0, s>>>(d_r, m, 1.0);
+    k_fill_d<<<grid_for(n, 256), 256, 0, s>>>(d_c, n, 1.0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int it = 0; it < ruiz_iters + (pock_chambolle ? 1 : 0); ++it) {
+        const bool pc = it >= ruiz_iters;
+        // both statistics from the same A~, then both factors updated
+        if (m > 0) {
+            if (pc) k_row_stat<true><<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
+            else k_row_stat<false><<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
+        }
+        if (pc) k_row_stat<true><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
+        else k_row_stat<false><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (m > 0) k_apply_scale<<<grid_for(m, 256), 256, 0, s>>>(d_r, tmp_r, m);
+        k_apply_scale<<<grid_for(n, 256), 256, 0, s>>>(d_c, tmp_c, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t scale_values(const Csr& a, const double* a_vals, const double* d_r, const double* d_c,
+                         bool rows_are_constraints, double* out64, float* out32, cudaStream_t s) {
+    if (a.rows == 0 || a.nnz == 0) return cudaSuccess;
+    k_scale_vals<<<grid_for((long long)a.rows * 32, 256), 256, 0, s>>>(a.rp, a.ci, a_vals, a.rows, d_r, d_c,
+                                                                         rows_are_constraints, out64, out32);
+    return cudaGetLastError();
+}
+
+cudaError_t scale_vectors(int m, int n, const double* d_r, const double* d_c, const double* c, const double* l,
+                          const double* u, const double* xl, const double* xu, double* cs, double* ls, double* us,
+                          double* xls, double* xus, cudaStream_t s) {
+    k_scale_vectors<<<grid_for(m > n ? m : n, 256), 256, 0, s>>>(m, n, d_r, d_c, c, l, u, xl, xu, cs, ls, us, xls, xus);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_f32(const double* in, float* out, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_to_f32<<<grid_for(count, 256), 256, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+static cudaError_t two_stage(const double* a, const double* b, int count, int mode, double* out_dev, double* part,
+                             cudaStream_t s) {
+    k_sum_stage1<<<kSumBlocks, kSumThreads, 0, s>>>(a, b, count, mode, part);
+    k_sum_stage2<<<1, kSumThreads, 0, s>>>(part, kSumBlocks, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t sq_norm(const double* v, int count, double* out_dev, cudaStream_t s) {
+    double* part = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&part, sizeof(double) * kSumBlocks, s);
+    if (e != cudaSuccess) return e;
+    if ((e = two_stage(v, nullptr, count, 0, out_dev, part, s)) != cudaSuccess) return e;
+    return cudaFreeAsync(part, s);
+}
+
+cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev, cudaStream_t s) {
+    double* part = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&part, sizeof(double) * kSumBlocks, s);
+    if (e != cudaSuccess) return e;
+    if ((e = two_stage(ls, us, m, 1, out_dev, part, s)) != cudaSuccess) return e;
+    return cudaFreeAsync(part, s);
+}
+
+// Power iteration on A~^T A~: sigma_est = ||A~ v|| for unit v.  Stops at the
+// first product where the estimate moves by <= tol relative, or when
+// ||A~^T A~ v|| = 0, or after max_iter products.  The host looks at the
+// history every kChunk products; products past the stopping point change
+// nothing that is returned.
+cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
+                       double* est_out, int* iters_out, cudaStream_t s) {
+    const int m = a.rows, n = a.cols;
+    // work layout: v (n), w (n), u (m), est2, nw2, v2, hist_est (max_iter+1), hist_nw (max_iter+1), part
+    double* v = work;
+    double* w = v + n;
+    double* u = w + n;
+    double* est2 = u + (m > 0 ? m : 1);
+    double* nw2 = est2 + 1;
+    double* v2 = nw2 + 1;
+    double* hist_est = v2 + 1;
+    double* hist_nw = hist_est + (max_iter + 1);
+    double* part = hist_nw + (max_iter + 1);
+    cudaError_t e;
+    *est_out = 0.0;
+    *iters_out = 0;
+    if (m == 0 || a.nnz == 0) return cudaSuccess;
+    k_power_init<<<grid_for(n, 256), 256, 0, s>>>(v, n, seed);
+    if ((e = two_stage(v, nullptr, n, 0, v2, part, s)) != cudaSuccess) return e;
+    k_power_normalize<<<grid_for(n, 256), 256, 0, s>>>(v, v, n, v2, v2, hist_est, hist_nw, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    constexpr int kChunk = 64;
+    std::vector<double> he(kChunk), hn(kChunk);
+    double prev = -1.0;
+    for (int base = 1; base <= max_iter; base += kChunk) {
+        const int last = base + kChunk - 1 < max_iter ? base + kChunk - 1 : max_iter;
+        for (int it = base; it <= last; ++it) {
+            k_spmv64<<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a.v64, m, v, u);
+            two_stage(u, nullptr, m, 0, est2, part, s);
+            k_spmv64<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at.v64, n, u, w);
+            two_stage(w, nullptr, n, 0, nw2, part, s);
+            k_power_normalize<<<grid_for(n, 256), 256, 0, s>>>(v, w, n, est2, nw2, hist_est, hist_nw, it);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int cnt = last - base + 1;
+        if ((e = cudaMemcpyAsync(he.data(), hist_est + base, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(hn.data(), hist_nw + base, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        for (int q = 0; q < cnt; ++q) {
+            const int it = base + q;
+            const double est = he[q];
+            *est_out = est;
+            *iters_out = it;
+            if (!(hn[q] > 0.0)) return cudaSuccess;
+            if (prev >= 0.0 && fabs(est - prev) <= tol * est) return cudaSuccess;
+            prev = est;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace lpb

@@ -1,0 +1,309 @@
+"""ctypes binding of liblpb.so (include/lpb.h): argument marshalling only.
+
+Every function named ``lpb_*`` here is the C entry point of the same name;
+the compute runs in the library's CUDA kernels.  There is no CPU fallback:
+importing this module without a built library, or calling it without a CUDA
+device, raises.
+
+``Handle`` / ``Batch`` are small conveniences over those calls for numpy
+inputs (CSR arrays, bound vectors, override records) and torch device
+tensors (the ``*_dev`` variant).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblpb.so")
+
+LPB_OK, LPB_ERR_INVALID_ARG, LPB_ERR_OOM, LPB_ERR_CUDA, LPB_ERR_TIMEOUT, LPB_ERR_DEVICE_CHECK, LPB_ERR_BAD_INDEX = range(7)
+ERR_NAMES = ["LPB_OK", "LPB_ERR_INVALID_ARG", "LPB_ERR_OOM", "LPB_ERR_CUDA", "LPB_ERR_TIMEOUT",
+             "LPB_ERR_DEVICE_CHECK", "LPB_ERR_BAD_INDEX"]
+OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITERATION_LIMIT, NUMERICAL = range(5)
+STATUS_NAMES = ["OPTIMAL", "PRIMAL_INFEASIBLE", "DUAL_INFEASIBLE", "ITERATION_LIMIT", "NUMERICAL"]
+FP64, MIXED = 0, 1
+
+# every symbol include/lpb.h declares
+EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
+           "lpb_result_device", "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_batch_free",
+           "lpb_destroy", "lpb_last_error"]
+
+
+class LpbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES[code] if 0 <= code < len(ERR_NAMES) else code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("check_every", C.c_int32), ("ruiz_iters", C.c_int32),
+                ("pock_chambolle", C.c_int32), ("beta_s", C.c_double), ("beta_n", C.c_double),
+                ("beta_a", C.c_double), ("theta", C.c_double), ("mnorm_sign", C.c_double),
+                ("restart_to_pdhg_output", C.c_int32), ("power_max_iter", C.c_int32),
+                ("power_tol", C.c_double), ("power_seed", C.c_uint64), ("eps_infeas", C.c_double),
+                ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("device", C.c_int32)]
+
+
+class Spec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("var", C.c_int32), ("lo", C.c_double), ("hi", C.c_double),
+                ("sign", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("restarts", C.c_int32), ("iters", C.c_int64), ("obj", C.c_double),
+                ("dual_obj", C.c_double), ("rel_primal", C.c_double), ("rel_dual", C.c_double),
+                ("rel_gap", C.c_double)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("bytes", C.c_double * 4),
+                ("setup_ms", C.c_double), ("checks", C.c_int64), ("compactions", C.c_int64),
+                ("kernels", C.c_int64)]
+
+
+SPEC_DTYPE = np.dtype([("kind", "<i4"), ("var", "<i4"), ("lo", "<f8"), ("hi", "<f8"), ("sign", "<f8")])
+assert SPEC_DTYPE.itemsize == C.sizeof(Spec)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblpb.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.lpb_default_options.argtypes = [C.POINTER(Options)]
+    lib.lpb_default_options.restype = None
+    lib.lpb_create.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Options), C.POINTER(vp)]
+    lib.lpb_solve.argtypes = [vp, i32, vp, d, i64, vp, vp, C.POINTER(vp)]
+    lib.lpb_solve_dev.argtypes = [vp, i32, vp, d, i64, vp, vp, C.POINTER(vp)]
+    lib.lpb_result.argtypes = [vp, i32, C.POINTER(Result), vp, vp]
+    lib.lpb_results.argtypes = [vp, vp]
+    lib.lpb_result_device.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+    lib.lpb_batch_profile.argtypes = [vp, C.POINTER(Profile)]
+    lib.lpb_handle_info.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i32)]
+    lib.lpb_scaling.argtypes = [vp, vp, vp]
+    lib.lpb_batch_free.argtypes = [vp]
+    lib.lpb_batch_free.restype = None
+    lib.lpb_destroy.argtypes = [vp]
+    lib.lpb_destroy.restype = None
+    lib.lpb_last_error.restype = C.c_char_p
+    for f in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results", "lpb_result_device",
+              "lpb_batch_profile", "lpb_handle_info", "lpb_scaling"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != LPB_OK:
+        raise LpbError(code, load().lpb_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+
+def lpb_default_options(**overrides) -> Options:
+    o = Options()
+    load().lpb_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def lpb_create(m, n, row_ptr, col_idx, vals, c, row_lo, row_hi, var_lo, var_hi, options: Options | None = None):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(vals, dtype=np.float64)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    cc, rl, ru, xl, xu = f(c), f(row_lo), f(row_hi), f(var_lo), f(var_hi)
+    h = C.c_void_p()
+    _check(load().lpb_create(int(m), int(n), int(rp[-1]), _ptr(rp), _ptr(ci) if ci.size else None,
+                             _ptr(va) if va.size else None, _ptr(cc), _ptr(rl) if rl.size else None,
+                             _ptr(ru) if ru.size else None, _ptr(xl), _ptr(xu),
+                             C.byref(options) if options is not None else None, C.byref(h)))
+    return h
+
+
+def lpb_solve(h, specs: np.ndarray, tol: float, max_iter: int, warm_x=None, warm_y=None):
+    sp = np.ascontiguousarray(specs, dtype=SPEC_DTYPE)
+    wx = None if warm_x is None else np.ascontiguousarray(warm_x, dtype=np.float64)
+    wy = None if warm_y is None else np.ascontiguousarray(warm_y, dtype=np.float64)
+    b = C.c_void_p()
+    _check(load().lpb_solve(h, int(sp.shape[0]), _ptr(sp) if sp.size else None, float(tol), int(max_iter),
+                            _ptr(wx), _ptr(wy), C.byref(b)))
+    return b
+
+
+def lpb_solve_dev(h, num_lps: int, specs_dev_ptr: int, tol: float, max_iter: int, warm_x_dev_ptr=None,
+                  warm_y_dev_ptr=None):
+    b = C.c_void_p()
+    _check(load().lpb_solve_dev(h, int(num_lps), specs_dev_ptr, float(tol), int(max_iter), warm_x_dev_ptr,
+                                warm_y_dev_ptr, C.byref(b)))
+    return b
+
+
+def lpb_result(b, lp: int, n: int, m: int, want_xy: bool = True):
+    r = Result()
+    x = np.zeros(n) if want_xy else None
+    y = np.zeros(max(m, 1)) if want_xy else None
+    _check(load().lpb_result(b, int(lp), C.byref(r), _ptr(x), _ptr(y)))
+    return r, x, (y[:m] if y is not None else None)
+
+
+def lpb_results(b, num_lps: int) -> np.ndarray:
+    out = (Result * max(num_lps, 1))()
+    _check(load().lpb_results(b, out))
+    arr = np.ctypeslib.as_array(out)[:num_lps]
+    return arr.copy()
+
+
+def lpb_result_device(b):
+    x, y = C.c_void_p(), C.c_void_p()
+    _check(load().lpb_result_device(b, C.byref(x), C.byref(y)))
+    return x.value, y.value
+
+
+def lpb_batch_profile(b) -> Profile:
+    p = Profile()
+    _check(load().lpb_batch_profile(b, C.byref(p)))
+    return p
+
+
+def lpb_handle_info(h):
+    eta, est, it = C.c_double(), C.c_double(), C.c_int32()
+    _check(load().lpb_handle_info(h, C.byref(eta), C.byref(est), C.byref(it)))
+    return eta.value, est.value, it.value
+
+
+def lpb_scaling(h, m: int, n: int):
+    dr, dc = np.zeros(max(m, 1)), np.zeros(n)
+    _check(load().lpb_scaling(h, _ptr(dr), _ptr(dc)))
+    return dr[:m], dc
+
+
+def lpb_batch_free(b) -> None:
+    load().lpb_batch_free(b)
+
+
+def lpb_destroy(h) -> None:
+    load().lpb_destroy(h)
+
+
+def lpb_last_error() -> str:
+    return load().lpb_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# conveniences
+# ---------------------------------------------------------------------------
+
+def specs_array(kind, var, lo=None, hi=None, sign=None) -> np.ndarray:
+    kind = np.asarray(kind)
+    a = np.zeros(kind.shape[0], dtype=SPEC_DTYPE)
+    a["kind"] = kind
+    a["var"] = var
+    a["lo"] = -np.inf if lo is None else lo
+    a["hi"] = np.inf if hi is None else hi
+    a["sign"] = 1.0 if sign is None else sign
+    return a
+
+
+def specs_from(s) -> np.ndarray:
+    """From any object with kind/var/lo/hi/sign arrays (e.g. lpgen.Specs)."""
+    return specs_array(s.kind, s.var, s.lo, s.hi, s.sign)
+
+
+class Batch:
+    def __init__(self, handle: "Handle", ptr):
+        self.h = handle
+        self.ptr = ptr
+        self.n, self.m = handle.n, handle.m
+
+    def results(self) -> np.ndarray:
+        return lpb_results(self.ptr, self.num_lps)
+
+    @property
+    def num_lps(self) -> int:
+        return self._num
+
+    def result(self, lp: int, want_xy: bool = True):
+        return lpb_result(self.ptr, lp, self.n, self.m, want_xy)
+
+    def device_xy(self):
+        return lpb_result_device(self.ptr)
+
+    def profile(self) -> Profile:
+        return lpb_batch_profile(self.ptr)
+
+    def free(self):
+        if self.ptr is not None:
+            lpb_batch_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Handle:
+    """One shared A with base vectors, resident on the GPU."""
+
+    def __init__(self, lp, options: Options | None = None, **opts):
+        if options is None:
+            options = lpb_default_options(**opts)
+        self.m, self.n = int(lp.m), int(lp.n)
+        self.options = options
+        self.ptr = lpb_create(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.vals, lp.c, lp.row_lo, lp.row_hi,
+                              lp.var_lo, lp.var_hi, options)
+
+    def solve(self, specs, tol: float = 1e-4, max_iter: int = 100000, warm_x=None, warm_y=None) -> Batch:
+        sp = specs if isinstance(specs, np.ndarray) else specs_from(specs)
+        b = Batch(self, lpb_solve(self.ptr, sp, tol, max_iter, warm_x, warm_y))
+        b._num = int(sp.shape[0])
+        return b
+
+    def solve_dev(self, specs_dev, tol: float = 1e-4, max_iter: int = 100000, warm_x=None, warm_y=None) -> Batch:
+        """specs_dev: a torch uint8 tensor on the handle's device holding
+        num_lps packed records (SPEC_DTYPE layout); warm_* torch float64
+        device tensors or None."""
+        num = specs_dev.numel() // SPEC_DTYPE.itemsize
+        b = Batch(self, lpb_solve_dev(self.ptr, num, specs_dev.data_ptr(), tol, max_iter,
+                                      None if warm_x is None else warm_x.data_ptr(),
+                                      None if warm_y is None else warm_y.data_ptr()))
+        b._num = num
+        return b
+
+    def info(self):
+        return lpb_handle_info(self.ptr)
+
+    def scaling(self):
+        return lpb_scaling(self.ptr, self.m, self.n)
+
+    def close(self):
+        if self.ptr is not None:
+            lpb_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

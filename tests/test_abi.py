@@ -1,0 +1,113 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads,
+exports every function include/lpb.h declares, and the ctypes mirrors of the
+header's structs have the header's sizes and offsets.  No compute calls."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lpb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_21990_gb300 import _build, lpb
+
+    _build.build()
+    return lpb.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:lpb_err|void|const char\*)\s+(lpb_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_expected_calls():
+    names = declared_functions()
+    for n in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_batch_free", "lpb_destroy",
+              "lpb_last_error", "lpb_default_options"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2601_21990_gb300 import lpb
+
+    assert sorted(lpb.EXPORTS) == declared_functions()
+
+
+def test_default_options(lib):
+    from paper_2601_21990_gb300 import lpb
+
+    o = lpb.lpb_default_options()
+    assert o.precision == lpb.MIXED and o.check_every == 64 and o.ruiz_iters == 10
+    assert (o.beta_s, o.beta_n, o.beta_a, o.theta, o.mnorm_sign) == (0.2, 0.8, 0.36, 0.5, -1.0)
+    assert o.device == -1 and o.cuda_stream is None
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_2601_21990_gb300 import lpb
+
+    src = tmp_path / "sz.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "lpb.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(lpb_options), sizeof(lpb_lp_spec), sizeof(lpb_lp_result), sizeof(lpb_profile));
+  printf("%zu %zu %zu\\n", offsetof(lpb_options, cuda_stream), offsetof(lpb_options, device), offsetof(lpb_profile, kernels));
+  return 0;
+}
+""")
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = [int(v) for v in out]
+    assert sizes[:4] == [ctypes.sizeof(lpb.Options), ctypes.sizeof(lpb.Spec), ctypes.sizeof(lpb.Result),
+                         ctypes.sizeof(lpb.Profile)]
+    assert sizes[4] == lpb.Options.cuda_stream.offset
+    assert sizes[5] == lpb.Options.device.offset
+    assert sizes[6] == lpb.Profile.kernels.offset
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    """Without a GPU the library returns an error code; nothing computes on
+    the CPU."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import lpgen
+    from paper_2601_21990_gb300 import lpb
+
+    w = lpgen.sb_small()
+    with pytest.raises(lpb.LpbError) as e:
+        lpb.Handle(w.lp)
+    assert e.value.code == lpb.LPB_ERR_CUDA
+
+
+def test_host_validation_rejects_bad_csr(lib):
+    """Argument checks run before any device call."""
+    import numpy as np
+
+    from paper_2601_21990_gb300 import lpb
+
+    inf = np.inf
+    ok = dict(m=1, n=2, row_ptr=[0, 2], col_idx=[0, 1], vals=[1.0, 1.0], c=[1.0, 1.0], row_lo=[0.0],
+              row_hi=[1.0], var_lo=[0.0, 0.0], var_hi=[1.0, 1.0])
+    bad = [dict(col_idx=[0, 2]), dict(vals=[1.0, np.nan]), dict(row_lo=[2.0]), dict(var_lo=[0.0, 2.0]),
+           dict(row_ptr=[1, 2]), dict(c=[inf, 1.0]), dict(row_lo=[inf]), dict(var_hi=[1.0, -inf])]
+    for b in bad:
+        kw = dict(ok)
+        kw.update(b)
+        with pytest.raises(lpb.LpbError) as e:
+            lpb.lpb_create(**kw)
+        assert e.value.code == lpb.LPB_ERR_INVALID_ARG, b

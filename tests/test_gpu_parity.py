@@ -1,0 +1,380 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Parity is on results, since LP optima x, y are in general not unique:
+  - per-LP status equals the oracle's;
+  - for OPTIMAL LPs, |f_gpu - f_ref| / (1 + |f_ref|) <= 1e-4 with f_ref the
+    oracle solved to 1e-7, and the oracle's own KKT routine applied to the
+    GPU's (x, y) gives rel. primal, dual and gap residuals <= 1e-4.
+The GPU runs at tol 1e-5 so that a 1e-4 objective bound has margin.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-4
+KKT_TOL = 1e-4
+GPU_TOL = 1e-5
+REF_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def lpb():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_21990_gb300 import _build, lpb as mod
+
+    _build.build()
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def oracle_ref(orc, lp, specs, tol=REF_TOL, **kw):
+    import os
+
+    return orc.solve(lp, specs, tol=tol, max_iter=400000, threads=os.cpu_count() or 1, lockstep=0, **kw)
+
+
+class _Ref:
+    def __init__(self, status, obj):
+        self.status = np.asarray(status, dtype=np.int32)
+        self.obj = np.asarray(obj, dtype=np.float64)
+
+
+def golden_ref(name):
+    """Oracle objectives at rel-KKT 1e-7 written by tests/golden/make_reference.py;
+    the file names the oracle source it came from."""
+    import hashlib
+    import json
+    import os
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    g = json.load(open(os.path.join(here, "golden", "reference_objectives.json")))
+    src = open(os.path.join(os.path.dirname(here), "oracle", "pdhg_oracle.c"), "rb").read()
+    assert g["oracle_sha256"] == hashlib.sha256(src).hexdigest(), "stale golden file: rerun make_reference.py"
+    c = g["cases"][name]
+    return _Ref(c["status"], c["obj"])
+
+
+def assert_parity(orc, lp, specs, batch, ref, kkt_lps=None, obj_tol=OBJ_TOL, kkt_tol=KKT_TOL):
+    res = batch.results()
+    np.testing.assert_array_equal(res["status"], ref.status)
+    opt = np.nonzero(ref.status == 0)[0]
+    err = np.abs(res["obj"][opt] - ref.obj[opt]) / (1.0 + np.abs(ref.obj[opt]))
+    assert err.size == 0 or err.max() <= obj_tol, (err.max(), opt[np.argmax(err)])
+    for q in (opt if kkt_lps is None else [q for q in kkt_lps if ref.status[q] == 0]):
+        r, x, y = batch.result(int(q))
+        k = orc.kkt_spec(lp, specs, int(q), x, y)
+        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= kkt_tol, (q, k)
+        # the library's own reported residuals agree with the oracle's evaluation
+        assert r.obj == pytest.approx(k["obj"], rel=1e-6, abs=1e-9)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sb_small(lpb, orc, precision):
+    w = lpgen.sb_small(seed=0)
+    ref = oracle_ref(orc, w.lp, w.specs)
+    h = lpb.Handle(w.lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    res = assert_parity(orc, w.lp, w.specs, b, ref)
+    assert np.all(res["iters"] % 64 == 0)
+
+
+def test_sb_powerlaw_full_size(lpb, orc):
+    """m=20k, n=50k, nnz~250k, B=64, FP32 iterates / FP64 checks: every LP."""
+    w = lpgen.sb_powerlaw(seed=0)
+    ref = golden_ref("sb_powerlaw_seed0")
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    assert_parity(orc, w.lp, w.specs, b, ref, kkt_lps=range(0, 64, 7))
+
+
+def test_sb_powerlaw_fp64_path(lpb, orc):
+    """The FP64 batched path on the same matrix (first 16 children)."""
+    w = lpgen.sb_powerlaw(seed=0)
+    idx = list(range(8)) + list(range(32, 40))
+    sp = w.specs.subset(idx)
+    full = golden_ref("sb_powerlaw_seed0")
+    ref = _Ref(full.status[idx], full.obj[idx])
+    h = lpb.Handle(w.lp, precision=lpb.FP64)
+    b = h.solve(sp, tol=GPU_TOL, max_iter=200000)
+    assert_parity(orc, w.lp, sp, b, ref, kkt_lps=[0, 9])
+
+
+def test_obbt_reduced(lpb, orc):
+    """Bound tightening with free variables at m=n=10k, 64 LPs (all columns)."""
+    w = lpgen.obbt_square(seed=0, m=10000, n=10000, lps=64)
+    ref = golden_ref("obbt_square_10k_seed0")
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    assert_parity(orc, w.lp, w.specs, b, ref, kkt_lps=[0, 33])
+
+
+def test_obbt_square_full_size_properties(lpb, orc):
+    """m=n=100k, nnz=1M, B=1024: at full size the oracle checks sampled
+    outputs one by one (KKT of the returned points) and properties that hold
+    at any size: min x_j <= x0_j <= max x_j for the feasible generating point
+    x0, both within the variable's box."""
+    w = lpgen.obbt_square(seed=0)
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    # the iteration cap of the paper's OBBT runs (Table 2: 100k iterations)
+    b = h.solve(w.specs, tol=1e-4, max_iter=100000)
+    res = b.results()
+    p = len(w.specs) // 2
+    assert np.all((res["status"] == 0) | (res["status"] == 3)), np.bincount(res["status"])
+    assert np.mean(res["status"] == 0) >= 0.5, np.bincount(res["status"])
+    for q in (0, 1, 511, 512, 700, 1023):
+        if res["status"][q] != 0:
+            continue
+        r, x, y = b.result(q)
+        k = orc.kkt_spec(w.lp, w.specs, q, x, y)
+        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-4, (q, k)
+    lo_obj, hi_obj = res["obj"][:p], -res["obj"][p:]
+    var = w.specs.var[:p]
+    ok = (res["status"][:p] == 0) & (res["status"][p:] == 0)
+    x0 = w.lp.x0[var]
+    scale = 1.0 + np.abs(x0)
+    assert np.all(lo_obj[ok] <= x0[ok] + 1e-3 * scale[ok])
+    assert np.all(hi_obj[ok] >= x0[ok] - 1e-3 * scale[ok])
+    assert np.all(lo_obj[ok] >= w.lp.var_lo[var][ok] - 1e-3 * scale[ok])
+    assert np.all(hi_obj[ok] <= w.lp.var_hi[var][ok] + 1e-3 * scale[ok])
+
+
+# ---------------------------------------------------------------------------
+# bound types, infeasibility, unboundedness
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_random_mixed_bound_lps(lpb, orc, precision):
+    """Small LPs with free, one-sided, fixed variables and equality, ranged,
+    one-sided rows; some infeasible, some unbounded.  Each solved as a batch
+    of its base LP plus strong-branching children."""
+    for seed in range(12):
+        feasible = seed % 3 != 2
+        lp = lpgen.random_lp(seed, 5 + seed % 4, 7 + seed % 3, feasible=feasible)
+        x0 = lp.x0
+        specs = lpgen.make_specs([0, 1, 1], [0, 1, 2], [-np.inf, np.ceil(x0[1]), -np.inf],
+                                 [np.inf, np.inf, np.floor(x0[2])])
+        ref = orc.solve(lp, specs, tol=1e-6, max_iter=400000, check_every=64)
+        h = lpb.Handle(lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED)
+        b = h.solve(specs, tol=1e-6 if precision == "fp64" else 1e-5, max_iter=400000)
+        res = b.results()
+        np.testing.assert_array_equal(res["status"], ref.status, err_msg=f"seed {seed}")
+        opt = ref.status == 0
+        err = np.abs(res["obj"][opt] - ref.obj[opt]) / (1 + np.abs(ref.obj[opt]))
+        assert err.size == 0 or err.max() <= 1e-4, (seed, err)
+
+
+def test_hand_infeasible_and_unbounded(lpb):
+    inf = np.inf
+    lp = lpgen.from_dense([[1, 1]], [1, 1], [3], [inf], [0, 0], [1, 1])
+    h = lpb.Handle(lp, precision=lpb.FP64)
+    assert h.solve(lpgen.base_specs(1), tol=1e-6).results()["status"][0] == 1
+    lp = lpgen.from_dense([[1, -1]], [-1, 0], [-inf], [1], [0, 0], [inf, inf])
+    h = lpb.Handle(lp, precision=lpb.FP64)
+    assert h.solve(lpgen.base_specs(1), tol=1e-6).results()["status"][0] == 2
+
+
+# ---------------------------------------------------------------------------
+# set-up pieces against the oracle
+# ---------------------------------------------------------------------------
+
+def test_scaling_and_step_size_match_oracle(lpb, orc):
+    w = lpgen.sb_powerlaw(seed=0)
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    dr, dc = h.scaling()
+    odr, odc = orc.scaling(w.lp)
+    np.testing.assert_allclose(dr, odr, rtol=1e-12)
+    np.testing.assert_allclose(dc, odc, rtol=1e-12)
+    eta, est, its = h.info()
+    rows = np.repeat(np.arange(w.lp.m), np.diff(w.lp.row_ptr))
+    scaled = lpgen.LPData(w.lp.m, w.lp.n, w.lp.row_ptr, w.lp.col_idx,
+                          odr[rows] * w.lp.vals * odc[w.lp.col_idx], w.lp.c, w.lp.row_lo, w.lp.row_hi,
+                          w.lp.var_lo, w.lp.var_hi)
+    oest, oits = orc.norm2_estimate(scaled)
+    assert est == pytest.approx(oest, rel=1e-8)
+    assert abs(its - oits) <= 2
+    assert eta == pytest.approx(0.998 / est, rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def _awkward_lp(seed=0):
+    """m=3000, n=300: one column in every row (a 3000-entry row of A^T, which
+    takes the merge-sort transpose path), a 150-entry column, two dense rows
+    longer than the long-row threshold, empty rows and an empty column."""
+    rng = np.random.default_rng(seed)
+    m, n = 3000, 300
+    rows, cols = [], []
+    for i in range(m):
+        k = rng.integers(1, 5)
+        cs = set(rng.choice(np.arange(2, n - 1), size=k, replace=False).tolist())
+        cs.add(0)
+        if i < 150:
+            cs.add(1)
+        if i in (7, 1234):
+            cs.update(range(2, n - 1))
+        if i in (5, 2999):
+            cs = set()
+        for j in sorted(cs):
+            rows.append(i)
+            cols.append(j)
+    rows, cols = np.array(rows), np.array(cols)
+    vals = np.where(rng.random(rows.size) < 0.5, -1.0, 1.0) * rng.uniform(0.1, 10, rows.size)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    x0 = rng.uniform(0, 10, n)
+    lp = lpgen.LPData(m, n, row_ptr, cols.astype(np.int32), vals, rng.normal(size=n), None, None,
+                      np.zeros(n), np.full(n, 10.0), x0, "awkward")
+    ax = lp.matvec(x0)
+    lp.row_lo = ax - rng.uniform(0, 1, m)
+    lp.row_hi = ax + rng.uniform(0, 1, m)
+    lp.row_lo[5], lp.row_hi[5] = -1.0, 1.0  # empty rows with 0 in range
+    return lp
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_awkward_structure(lpb, orc, precision):
+    lp = _awkward_lp()
+    cand = np.array([0, 1, 3, 50, 298])
+    specs = lpgen.sb_specs(lp.x0, cand)
+    ref = oracle_ref(orc, lp, specs)
+    h = lpb.Handle(lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED)
+    b = h.solve(specs, tol=GPU_TOL, max_iter=400000)
+    assert_parity(orc, lp, specs, b, ref)
+
+
+def test_ragged_and_multi_tile_batches(lpb, orc):
+    """13 LPs (not a multiple of the vector width) and 200 LPs (two column
+    tiles of the FP64 kernels, repeated children) give the same per-LP
+    objectives as the oracle."""
+    w = lpgen.sb_small(seed=1)
+    ref16 = oracle_ref(orc, w.lp, w.specs)
+    h = lpb.Handle(w.lp, precision=lpb.FP64)
+    b13 = h.solve(w.specs.subset(range(13)), tol=GPU_TOL, max_iter=200000).results()
+    np.testing.assert_array_equal(b13["status"], ref16.status[:13])
+    assert np.max(np.abs(b13["obj"] - ref16.obj[:13]) / (1 + np.abs(ref16.obj[:13]))) <= OBJ_TOL
+    idx = np.arange(200) % 16
+    b200 = h.solve(w.specs.subset(idx), tol=GPU_TOL, max_iter=200000).results()
+    np.testing.assert_array_equal(b200["status"], ref16.status[idx])
+    assert np.max(np.abs(b200["obj"] - ref16.obj[idx]) / (1 + np.abs(ref16.obj[idx]))) <= OBJ_TOL
+
+
+def test_box_lp_without_rows(lpb):
+    rng = np.random.default_rng(4)
+    n = 37
+    lo = rng.uniform(-5, 0, n)
+    hi = lo + rng.uniform(0.5, 4, n)
+    c = rng.normal(size=n)
+    lp = lpgen.from_dense(np.zeros((0, n)), c, [], [], lo, hi)
+    h = lpb.Handle(lp, precision=lpb.FP64)
+    b = h.solve(lpgen.base_specs(1), tol=1e-9, max_iter=10000)
+    r, x, y = b.result(0)
+    assert r.status == 0
+    np.testing.assert_allclose(x, np.where(c > 0, lo, hi), atol=1e-8)
+    cand = np.arange(n)
+    ro = h.solve(lpgen.obbt_specs(cand), tol=1e-9, max_iter=10000).results()
+    np.testing.assert_allclose(ro["obj"][:n], lo, atol=1e-7)
+    np.testing.assert_allclose(-ro["obj"][n:], hi, atol=1e-7)
+
+
+def test_empty_batch_empty_box_and_iteration_limit(lpb):
+    w = lpgen.sb_small()
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    b = h.solve(lpgen.base_specs(0), tol=1e-4)
+    assert b.results().shape == (0,)
+    sp = lpgen.make_specs([1, 0, 1], [3, 0, 4], [5.0, -np.inf, 9.5], [4.0, np.inf, np.inf])
+    res = h.solve(sp, tol=1e-4).results()
+    assert res["status"][0] == 1 and res["iters"][0] == 0
+    assert res["status"][1] == 0
+    lim = h.solve(w.specs.subset([0, 1]), tol=1e-12, max_iter=1).results()
+    assert np.all(lim["status"] == 3) and np.all(lim["iters"] == 1)
+    lim = h.solve(w.specs.subset([0, 1]), tol=1e-12, max_iter=100).results()
+    assert np.all(lim["status"] == 3) and np.all(lim["iters"] == 100)
+
+
+def test_bad_override_index_is_rejected(lpb):
+    import torch
+
+    w = lpgen.sb_small()
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    sp = lpgen.make_specs([1], [w.lp.n], [1.0], [np.inf])
+    with pytest.raises(lpb.LpbError) as e:
+        h.solve(sp, tol=1e-4)
+    assert e.value.code == lpb.LPB_ERR_BAD_INDEX
+    dev = torch.from_numpy(lpb.specs_from(sp).view(np.uint8).copy()).cuda()
+    with pytest.raises(lpb.LpbError) as e:
+        h.solve_dev(dev, tol=1e-4)
+    assert e.value.code == lpb.LPB_ERR_BAD_INDEX
+    # the handle stays usable
+    assert h.solve(w.specs.subset([0]), tol=1e-4).results()["status"][0] == 0
+
+
+def test_deterministic(lpb):
+    w = lpgen.sb_powerlaw(seed=0)
+    sp = w.specs.subset(range(20))
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    a = h.solve(sp, tol=1e-4).results()
+    b = h.solve(sp, tol=1e-4).results()
+    np.testing.assert_array_equal(a["obj"], b["obj"])
+    np.testing.assert_array_equal(a["iters"], b["iters"])
+    h2 = lpb.Handle(w.lp, precision=lpb.MIXED)
+    c = h2.solve(sp, tol=1e-4).results()
+    np.testing.assert_array_equal(a["obj"], c["obj"])
+
+
+def test_batch_result_equals_alone(lpb):
+    """Each LP solved alone (B=1, own restarts) gives the same objective as
+    inside the batch (batch-averaged restarts), within tolerance."""
+    w = lpgen.sb_small(seed=2)
+    h = lpb.Handle(w.lp, precision=lpb.FP64)
+    batch = h.solve(w.specs, tol=1e-7, max_iter=400000).results()
+    for q in range(0, 16, 3):
+        alone = h.solve(w.specs.subset([q]), tol=1e-7, max_iter=400000).results()
+        assert alone["status"][0] == batch["status"][q]
+        assert abs(alone["obj"][0] - batch["obj"][q]) / (1 + abs(batch["obj"][q])) <= 1e-5
+
+
+def test_warm_start(lpb):
+    w = lpgen.sb_small(seed=0)
+    h = lpb.Handle(w.lp, precision=lpb.FP64)
+    cold = h.solve(w.specs, tol=1e-6, max_iter=200000)
+    rc = cold.results()
+    xs = np.stack([cold.result(q)[1] for q in range(16)])
+    ys = np.stack([cold.result(q)[2] for q in range(16)])
+    warm = h.solve(w.specs, tol=1e-6, max_iter=200000, warm_x=xs, warm_y=ys).results()
+    np.testing.assert_array_equal(warm["status"], rc["status"])
+    assert np.max(np.abs(warm["obj"] - rc["obj"]) / (1 + np.abs(rc["obj"]))) <= 1e-5
+    assert warm["iters"].sum() < rc["iters"].sum()
+
+
+def test_device_path_matches_host_path(lpb):
+    import torch
+
+    w = lpgen.sb_small(seed=0)
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    a = h.solve(w.specs, tol=1e-5).results()
+    dev = torch.from_numpy(lpb.specs_from(w.specs).view(np.uint8).copy()).cuda()
+    b = h.solve_dev(dev, tol=1e-5)
+    np.testing.assert_array_equal(a["obj"], b.results()["obj"])
+    xd, yd = b.device_xy()
+    assert xd and yd
