@@ -290,7 +290,7 @@ def main():
         b.free()
     torch.cuda.synchronize()
     b1_s = time.perf_counter() - t0
-    b1_value = b1_solved / b1_s
+    b1_value = b1_solved / b1_s if b1_n > 0 else None
 
     # end to end through the public host API: create (H2D of A, vectors),
     # solve from host records, results back to the host
@@ -333,7 +333,8 @@ def main():
                          "other_kernel_GBps": by[1 - dom] / (ms[1 - dom] / 1e3) / 1e9 if ms[1 - dom] > 0 else None},
             "time_split_ms_per_step": {"primal_step": ms[0] / args.steps, "dual_step": ms[1] / args.steps,
                                        "check_spmm": ms[2] / args.steps, "check_reduce": ms[3] / args.steps},
-            "b1_loop": {"value": b1_value, "unit": UNIT, "lps": b1_n, "batched_over_b1": value / world / b1_value},
+            "b1_loop": {"value": b1_value, "unit": UNIT, "lps": b1_n,
+                        "batched_over_b1": value / world / b1_value if b1_value else None},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "what": "one batched solve"},
             "cpu_baseline": cpu,

@@ -75,6 +75,10 @@ typedef struct {
     int32_t profile;                /* 1: time every iteration kernel with CUDA events */
     void* cuda_stream;              /* cudaStream_t to run on, or NULL */
     int32_t device;                 /* CUDA device ordinal, or -1 for the current device */
+    int32_t fp64_polish;            /* LPB_MIXED only: 1 (default) widens the remaining batch to FP64
+                                       iterates once an LP stalls at FP32 resolution */
+    int32_t polish_stall_checks;    /* an LP stalls when its KKT error has not halved over this many
+                                       checks (default 32) */
 } lpb_options;
 
 /* One override record (Sec. 5.1, 5.2). */
@@ -109,6 +113,7 @@ typedef struct {
     double setup_ms;      /* lpb_create device work */
     int64_t checks, compactions;
     int64_t kernels;      /* every kernel the solve launched */
+    int64_t fp64_switch_iter;  /* iteration at which the batch moved to FP64 iterates, -1 if never */
 } lpb_profile;
 
 /* Fills *opt with the defaults listed above. */

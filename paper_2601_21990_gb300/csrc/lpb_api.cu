@@ -62,18 +62,27 @@ struct lpb_ctx {
     double *c = nullptr, *l = nullptr, *u = nullptr, *xl = nullptr, *xu = nullptr;
     double *cs = nullptr, *ls = nullptr, *us = nullptr, *xls = nullptr, *xus = nullptr;
     float *cs32 = nullptr, *ls32 = nullptr, *us32 = nullptr, *xls32 = nullptr, *xus32 = nullptr;
+    // double-float copies for the checks of FP32 iterates
+    df *f_dr = nullptr, *f_dc = nullptr, *f_idr = nullptr, *f_idc = nullptr, *f_c = nullptr;
+    df *f_xl = nullptr, *f_xu = nullptr, *f_l = nullptr, *f_u = nullptr;
     double eta = 0.0, norm_est = 0.0, c_norm_base = 0.0, b_norm = 0.0, setup_ms = 0.0;
     int power_iters = 0;
     std::vector<void*> fixed_allocs;
     // per-capacity workspace
     int cap = 0, ld = 0;
     std::vector<void*> ws_allocs;
-    void *X = nullptr, *X0 = nullptr, *Xbar = nullptr, *Xh = nullptr, *DX = nullptr, *G = nullptr;
-    void *Y = nullptr, *Y0 = nullptr, *Yh = nullptr, *DY = nullptr, *DYp = nullptr;
+    // iterate buffers and per-column parameters in each precision: [0] FP32
+    // (mixed path), [1] FP64 (FP64 path, and the mixed path's FP64 polish)
+    struct Set {
+        void *X = nullptr, *X0 = nullptr, *Xbar = nullptr, *Xh = nullptr, *DX = nullptr;
+        void *Y = nullptr, *Y0 = nullptr, *Yh = nullptr, *DY = nullptr, *DYp = nullptr;
+        void *clo = nullptr, *chi = nullptr, *cc = nullptr, *ctau = nullptr, *csigma = nullptr;
+    } set[2];
     double *P = nullptr, *Q = nullptr, *partials = nullptr, *colsum = nullptr;
-    int *ckind = nullptr, *cvar = nullptr, *clp = nullptr;
-    void *clo = nullptr, *chi = nullptr, *cc = nullptr, *ctau = nullptr, *csigma = nullptr;
-    double *k_lo = nullptr, *k_hi = nullptr, *k_c = nullptr, *k_w = nullptr;
+    int *ckind = nullptr, *cvar = nullptr, *clp = nullptr, *k_stall = nullptr;
+    double *k_lo = nullptr, *k_hi = nullptr, *k_c = nullptr, *k_w = nullptr, *k_best = nullptr;
+    double* hal64 = nullptr;   // Halpern weights of the next interval
+    float* hal32 = nullptr;
     ColRecord* rec = nullptr;
     Control* ctl = nullptr;
     int* mv = nullptr;
@@ -120,19 +129,27 @@ void free_workspace(lpb_ctx* h) {
     h->cap = h->ld = 0;
 }
 
+bool polish_enabled(const lpb_ctx* h) { return h->opt.precision == LPB_MIXED && h->opt.fp64_polish; }
+
 lpb_err ensure_workspace(lpb_ctx* h, int num_lps) {
     if (num_lps <= h->cap) return LPB_OK;
     free_workspace(h);
     const int cap = (int)rup((size_t)num_lps, 4);
     const int ld = cap;
-    const size_t tsz = h->opt.precision == LPB_MIXED ? sizeof(float) : sizeof(double);
     const size_t mr = h->m > 0 ? (size_t)h->m : 1;
-    const size_t nx = (size_t)h->n * ld * tsz, ny = mr * ld * tsz;
     auto& L = h->ws_allocs;
-    void** xs[] = {&h->X, &h->X0, &h->Xbar, &h->Xh, &h->DX, &h->G};
-    for (void** p : xs) CU(dmalloc(L, (char**)p, nx));
-    void** ys[] = {&h->Y, &h->Y0, &h->Yh, &h->DY, &h->DYp};
-    for (void** p : ys) CU(dmalloc(L, (char**)p, ny));
+    for (int p = 0; p < 2; ++p) {
+        const bool need = p == 1 ? (h->opt.precision == LPB_FP64 || polish_enabled(h)) : h->opt.precision == LPB_MIXED;
+        if (!need) continue;
+        const size_t tsz = p == 0 ? sizeof(float) : sizeof(double);
+        auto& S = h->set[p];
+        void** xs[] = {&S.X, &S.X0, &S.Xbar, &S.Xh, &S.DX};
+        for (void** q : xs) CU(dmalloc(L, (char**)q, (size_t)h->n * ld * tsz));
+        void** ys[] = {&S.Y, &S.Y0, &S.Yh, &S.DY, &S.DYp};
+        for (void** q : ys) CU(dmalloc(L, (char**)q, mr * ld * tsz));
+        void** cs[] = {&S.clo, &S.chi, &S.cc, &S.ctau, &S.csigma};
+        for (void** q : cs) CU(dmalloc(L, (char**)q, tsz * ld));
+    }
     CU(dmalloc(L, &h->P, sizeof(double) * 2 * mr * ld));
     CU(dmalloc(L, &h->Q, sizeof(double) * 3 * (size_t)h->n * ld));
     CU(dmalloc(L, &h->partials, sizeof(double) * (size_t)kNumStats * kReduceBlocks * ld));
@@ -140,12 +157,14 @@ lpb_err ensure_workspace(lpb_ctx* h, int num_lps) {
     CU(dmalloc(L, &h->ckind, sizeof(int) * ld));
     CU(dmalloc(L, &h->cvar, sizeof(int) * ld));
     CU(dmalloc(L, &h->clp, sizeof(int) * ld));
-    void** cs[] = {&h->clo, &h->chi, &h->cc, &h->ctau, &h->csigma};
-    for (void** p : cs) CU(dmalloc(L, (char**)p, tsz * ld));
+    CU(dmalloc(L, &h->k_stall, sizeof(int) * ld));
     CU(dmalloc(L, &h->k_lo, sizeof(double) * ld));
     CU(dmalloc(L, &h->k_hi, sizeof(double) * ld));
     CU(dmalloc(L, &h->k_c, sizeof(double) * ld));
     CU(dmalloc(L, &h->k_w, sizeof(double) * ld));
+    CU(dmalloc(L, &h->k_best, sizeof(double) * ld));
+    CU(dmalloc(L, &h->hal64, sizeof(double) * 2 * (size_t)h->opt.check_every));
+    CU(dmalloc(L, &h->hal32, sizeof(float) * 2 * (size_t)h->opt.check_every));
     CU(dmalloc(L, &h->rec, sizeof(ColRecord) * ld));
     CU(dmalloc(L, &h->ctl, sizeof(Control)));
     CU(dmalloc(L, &h->mv, sizeof(int) * 4 * ld));
@@ -158,46 +177,49 @@ lpb_err ensure_workspace(lpb_ctx* h, int num_lps) {
     return LPB_OK;
 }
 
-template <typename T> const T* pick(const lpb_ctx*, const double* d64, const float* d32);
-template <> const double* pick<double>(const lpb_ctx*, const double* d64, const float*) { return d64; }
-template <> const float* pick<float>(const lpb_ctx*, const double*, const float* d32) { return d32; }
+template <typename T> const T* pick(const double* d64, const float* d32);
+template <> const double* pick<double>(const double* d64, const float*) { return d64; }
+template <> const float* pick<float>(const double*, const float* d32) { return d32; }
+template <typename T> constexpr int set_of() { return sizeof(T) == sizeof(float) ? 0 : 1; }
 
 template <typename T>
 IterData<T> iter_data(const lpb_ctx* h) {
+    const auto& S = h->set[set_of<T>()];
     IterData<T> d{};
     d.A = h->A;
     d.At = h->At;
-    d.a_vals = pick<T>(h, h->A.v64, h->A.v32);
-    d.at_vals = pick<T>(h, h->At.v64, h->At.v32);
-    d.c = pick<T>(h, h->cs, h->cs32);
-    d.xl = pick<T>(h, h->xls, h->xls32);
-    d.xu = pick<T>(h, h->xus, h->xus32);
-    d.l = pick<T>(h, h->ls, h->ls32);
-    d.u = pick<T>(h, h->us, h->us32);
+    d.a_vals = pick<T>(h->A.v64, h->A.v32);
+    d.at_vals = pick<T>(h->At.v64, h->At.v32);
+    d.c = pick<T>(h->cs, h->cs32);
+    d.xl = pick<T>(h->xls, h->xls32);
+    d.xu = pick<T>(h->xus, h->xus32);
+    d.l = pick<T>(h->ls, h->ls32);
+    d.u = pick<T>(h->us, h->us32);
     d.col.kind = h->ckind;
     d.col.var = h->cvar;
-    d.col.lo = (T*)h->clo;
-    d.col.hi = (T*)h->chi;
-    d.col.c = (T*)h->cc;
-    d.col.tau = (T*)h->ctau;
-    d.col.sigma = (T*)h->csigma;
+    d.col.lo = (T*)S.clo;
+    d.col.hi = (T*)S.chi;
+    d.col.c = (T*)S.cc;
+    d.col.tau = (T*)S.ctau;
+    d.col.sigma = (T*)S.csigma;
     return d;
 }
 
 template <typename T>
 IterBufs<T> iter_bufs(const lpb_ctx* h) {
+    const auto& S = h->set[set_of<T>()];
     IterBufs<T> b{};
-    b.X = (T*)h->X;
-    b.X0 = (T*)h->X0;
-    b.Xbar = (T*)h->Xbar;
-    b.Y = (T*)h->Y;
-    b.Y0 = (T*)h->Y0;
-    b.Xh = (T*)h->Xh;
-    b.DX = (T*)h->DX;
-    b.G = (T*)h->G;
-    b.Yh = (T*)h->Yh;
-    b.DY = (T*)h->DY;
-    b.DYp = (T*)h->DYp;
+    b.X = (T*)S.X;
+    b.X0 = (T*)S.X0;
+    b.Xbar = (T*)S.Xbar;
+    b.Y = (T*)S.Y;
+    b.Y0 = (T*)S.Y0;
+    b.Xh = (T*)S.Xh;
+    b.DX = (T*)S.DX;
+    b.G = nullptr;
+    b.Yh = (T*)S.Yh;
+    b.DY = (T*)S.DY;
+    b.DYp = (T*)S.DYp;
     return b;
 }
 
@@ -221,6 +243,8 @@ CheckData check_data(const lpb_ctx* h, double tol) {
     d.col.c = h->k_c;
     d.col.w = h->k_w;
     d.col.lp = h->clp;
+    d.col.best = h->k_best;
+    d.col.stall = h->k_stall;
     d.eta = h->eta;
     d.beta_s = h->opt.beta_s;
     d.beta_n = h->opt.beta_n;
@@ -231,16 +255,30 @@ CheckData check_data(const lpb_ctx* h, double tol) {
     d.tol = tol;
     d.detect_inf = h->opt.detect_infeasibility;
     d.restart_to_output = h->opt.restart_to_pdhg_output;
+    d.stall_checks = 0;
+    d.check_every = h->opt.check_every;
+    d.hal64 = h->hal64;
+    d.hal32 = h->hal32;
+    d.f_dr = h->f_dr;
+    d.f_dc = h->f_dc;
+    d.f_idr = h->f_idr;
+    d.f_idc = h->f_idc;
+    d.f_c = h->f_c;
+    d.f_xl = h->f_xl;
+    d.f_xu = h->f_xu;
+    d.f_l = h->f_l;
+    d.f_u = h->f_u;
     return d;
 }
 
-double step_bytes(const lpb_ctx* h, bool primal, bool check, int ncol) {
-    const double ts = h->opt.precision == LPB_MIXED ? 4.0 : 8.0;
-    const double rows = primal ? h->n : h->m, cols = primal ? h->m : h->n;
-    double b = (4.0 + ts) * h->nnz + 4.0 * (rows + 1);
+double step_bytes(bool fp32, int nnz, int m, int n, bool primal, bool check, int ncol) {
+    const double ts = fp32 ? 4.0 : 8.0;
+    const double rows = primal ? n : m, cols = primal ? m : n;
+    double b = (4.0 + ts) * nnz + 4.0 * (rows + 1);
     // gathered block once, plus the row-side operands: primal reads X, X0 and
-    // writes X, Xbar; dual reads Y, Y0 and writes Y; a check writes 3 more
-    b += ts * ncol * (cols + rows * (primal ? 4.0 : 3.0) + (check ? 3.0 * rows : 0.0));
+    // writes X, Xbar; dual reads Y, Y0 and writes Y; a check writes x^, dx
+    // (primal) or y^, dy, Pi_B(dy) (dual)
+    b += ts * ncol * (cols + rows * (primal ? 4.0 : 3.0) + (check ? (primal ? 2.0 : 3.0) * rows : 0.0));
     return b;
 }
 
@@ -255,9 +293,18 @@ void set_result(lpb_lp_result& r, const ColRecord& rc, int status, int64_t iters
     r.rel_gap = rc.rel_gap;
 }
 
+// State of one solve that survives a change of iterate precision.
+struct SolveState {
+    std::vector<int> colmap;  // column -> LP index
+    int ncol = 0;
+    int64_t K = 0;            // iterations done
+    bool done = false;
+};
+
 template <typename T>
-lpb_err compact(lpb_ctx* h, std::vector<int>& colmap, const std::vector<int>& fin, int& ncol, lpb_profile& prof) {
+lpb_err compact(lpb_ctx* h, SolveState& st, const std::vector<int>& fin, lpb_profile& prof) {
     if (fin.empty()) return LPB_OK;
+    const int ncol = st.ncol;
     std::vector<char> is_fin(ncol, 0);
     for (int f : fin) is_fin[f] = 1;
     const int ncol2 = ncol - (int)fin.size();
@@ -269,11 +316,11 @@ lpb_err compact(lpb_ctx* h, std::vector<int>& colmap, const std::vector<int>& fi
         while (is_fin[tail]) --tail;
         src[cnt] = tail;
         dst[cnt] = f;
-        colmap[f] = colmap[tail];
+        st.colmap[f] = st.colmap[tail];
         ++cnt;
         --tail;
     }
-    ncol = ncol2;
+    st.ncol = ncol2;
     if (cnt == 0) return LPB_OK;
     CU(cudaMemcpyAsync(h->mv, src, sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->mv + h->ld, dst, sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
@@ -285,75 +332,43 @@ lpb_err compact(lpb_ctx* h, std::vector<int>& colmap, const std::vector<int>& fi
     return LPB_OK;
 }
 
+// Runs checked intervals in precision T until the batch is done, max_iter is
+// reached, or (FP32 with polish enabled) an LP stalls.  Returns with
+// st.done = false only in the last case.
 template <typename T>
-lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double tol, int64_t max_iter,
-                   const double* wx, const double* wy, lpb_batch* bt) {
+lpb_err run_phase(lpb_ctx* h, SolveState& st, double tol, int64_t max_iter, lpb_batch* bt) {
     lpb_err rc;
-    if ((rc = ensure_workspace(h, num_lps)) != LPB_OK) return rc;
     cudaStream_t s = h->stream;
-    const int n = h->n, m = h->m, ld = h->ld;
-    CU(cudaMalloc((void**)&bt->x, sizeof(double) * (size_t)n * (num_lps ? num_lps : 1)));
-    CU(cudaMalloc((void**)&bt->y, sizeof(double) * (size_t)(m ? m : 1) * (num_lps ? num_lps : 1)));
-    CU(cudaMemsetAsync(bt->x, 0, sizeof(double) * (size_t)n * num_lps, s));
-    CU(cudaMemsetAsync(bt->y, 0, sizeof(double) * (size_t)m * num_lps, s));
-    bt->res.assign(num_lps, lpb_lp_result{});
-    if (num_lps == 0) {
-        CU(cudaStreamSynchronize(s));
-        return LPB_OK;
-    }
+    const int m = h->m, ld = h->ld;
     IterData<T> id = iter_data<T>(h);
     IterBufs<T> ib = iter_bufs<T>(h);
     CheckData cd = check_data(h, tol);
+    const bool can_promote = sizeof(T) == sizeof(float) && polish_enabled(h);
+    if (can_promote) cd.stall_checks = h->opt.polish_stall_checks;
     lpb_profile& prof = bt->prof;
-    prof.setup_ms = h->setup_ms;
     const bool profile = h->opt.profile != 0;
     const int ce = h->opt.check_every;
-    if (profile && (int)h->events.size() < 3 * ce + 3) {
-        for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-        h->events.assign(3 * ce + 3, nullptr);
-        for (auto& e : h->events) CU(cudaEventCreate(&e));
-    }
-
-    CU(launch_init<T>(cd, id, ib, ld, num_lps, specs_dev, wx, wy, h->c_norm_base, h->b_norm, h->rec, h->ctl, s));
-    prof.kernels += 3;
-    CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * num_lps, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (h->ctl_h->error) {
-        const int code = h->ctl_h->error;
-        return fail((lpb_err)code, code == LPB_ERR_BAD_INDEX ? "an override names a variable outside [0, n)"
-                                                              : "an override record has an invalid kind or value");
-    }
-    std::vector<int> colmap(num_lps);
-    for (int j = 0; j < num_lps; ++j) colmap[j] = j;
-    int ncol = num_lps;
+    const bool fp32 = sizeof(T) == sizeof(float);
     std::vector<int> fin;
-    for (int j = 0; j < num_lps; ++j)
-        if (h->rec_h[j].status >= 0) {
-            set_result(bt->res[j], h->rec_h[j], h->rec_h[j].status, 0, 0);
-            fin.push_back(j);
-        }
-    if ((rc = compact<T>(h, colmap, fin, ncol, prof)) != LPB_OK) return rc;
-
-    int64_t K = 0;
-    while (ncol > 0 && K < max_iter) {
-        const int L = (int)std::min<int64_t>(ce, max_iter - K);
+    while (st.ncol > 0 && st.K < max_iter) {
+        const int L = (int)std::min<int64_t>(ce, max_iter - st.K);
         for (int t = 0; t < L; ++t) {
             const bool chk = t == L - 1;
-            CU(launch_iteration<T>(id, ib, ld, ncol, &h->ctl->k, t, chk, s, profile ? &h->events[3 * t] : nullptr));
+            CU(launch_iteration<T>(id, ib, ld, st.ncol, pick<T>(h->hal64, h->hal32), t, chk, s,
+                                   profile ? &h->events[3 * t] : nullptr));
             prof.launches[0] += 1;
             prof.launches[1] += m > 0 ? 1 : 0;
             prof.kernels += m > 0 ? 2 : 1;
-            prof.bytes[0] += step_bytes(h, true, chk, ncol);
-            prof.bytes[1] += step_bytes(h, false, chk, ncol);
+            prof.bytes[0] += step_bytes(fp32, h->nnz, m, h->n, true, chk, st.ncol);
+            prof.bytes[1] += step_bytes(fp32, h->nnz, m, h->n, false, chk, st.ncol);
         }
-        CU(launch_check<T>(cd, ib, ld, ncol, K + L - 1, L, K + L == max_iter, h->P, h->Q, h->partials, h->colsum,
-                           h->rec, h->ctl, id.col, s, profile ? &h->events[3 * L] : nullptr));
+        CU(launch_check<T>(cd, ib, ld, st.ncol, st.K + L - 1, L, st.K + L == max_iter, h->P, h->Q, h->partials,
+                           h->colsum, h->rec, h->ctl, id.col, s, profile ? &h->events[3 * L] : nullptr));
         prof.launches[2] += m > 0 ? 2 : 1;
         prof.launches[3] += 1;
         prof.checks += 1;
         prof.kernels += (m > 0 ? 2 : 1) + (m > 0 ? 1 : 0) + 1 + 1 + 1 + (m > 0 ? 2 : 1);
-        CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * ncol, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * st.ncol, cudaMemcpyDeviceToHost, s));
         CU(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         if (profile) {
@@ -369,14 +384,14 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
             CU(cudaEventElapsedTime(&ms, h->events[3 * L + 1], h->events[3 * L + 2]));
             prof.ms[3] += ms;
         }
-        K += L;
+        st.K += L;
         const int64_t restarts_before = h->ctl_h->restarts - h->ctl_h->restart;
         fin.clear();
-        for (int j = 0; j < ncol; ++j) {
-            int st = h->rec_h[j].status;
-            if (st < 0 && K >= max_iter) st = LPB_ITERATION_LIMIT;
-            if (st >= 0) {
-                set_result(bt->res[colmap[j]], h->rec_h[j], st, K, restarts_before);
+        for (int j = 0; j < st.ncol; ++j) {
+            int sj = h->rec_h[j].status;
+            if (sj < 0 && st.K >= max_iter) sj = LPB_ITERATION_LIMIT;
+            if (sj >= 0) {
+                set_result(bt->res[st.colmap[j]], h->rec_h[j], sj, st.K, restarts_before);
                 fin.push_back(j);
             }
         }
@@ -385,15 +400,78 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
             int* lps = h->mv_h + 3 * ld;
             for (size_t q = 0; q < fin.size(); ++q) {
                 cols[q] = fin[q];
-                lps[q] = colmap[fin[q]];
+                lps[q] = st.colmap[fin[q]];
             }
             const int cnt = (int)fin.size();
             CU(cudaMemcpyAsync(h->mv + 2 * ld, cols, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
             CU(cudaMemcpyAsync(h->mv + 3 * ld, lps, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
             CU(launch_extract<T>(cd, ib, ld, h->mv + 2 * ld, h->mv + 3 * ld, cnt, h->xl, h->xu, bt->x, bt->y, s));
             prof.kernels += 1;
-            if ((rc = compact<T>(h, colmap, fin, ncol, prof)) != LPB_OK) return rc;
+            if ((rc = compact<T>(h, st, fin, prof)) != LPB_OK) return rc;
         }
+        if (can_promote && h->ctl_h->stalled && st.ncol > 0 && st.K < max_iter) return LPB_OK;
+    }
+    st.done = true;
+    return LPB_OK;
+}
+
+template <typename T>
+lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double tol, int64_t max_iter,
+                   const double* wx, const double* wy, lpb_batch* bt) {
+    lpb_err rc;
+    if ((rc = ensure_workspace(h, num_lps)) != LPB_OK) return rc;
+    cudaStream_t s = h->stream;
+    const int n = h->n, m = h->m, ld = h->ld;
+    CU(cudaMalloc((void**)&bt->x, sizeof(double) * (size_t)n * (num_lps ? num_lps : 1)));
+    CU(cudaMalloc((void**)&bt->y, sizeof(double) * (size_t)(m ? m : 1) * (num_lps ? num_lps : 1)));
+    CU(cudaMemsetAsync(bt->x, 0, sizeof(double) * (size_t)n * num_lps, s));
+    CU(cudaMemsetAsync(bt->y, 0, sizeof(double) * (size_t)m * num_lps, s));
+    bt->res.assign(num_lps, lpb_lp_result{});
+    lpb_profile& prof = bt->prof;
+    prof.setup_ms = h->setup_ms;
+    prof.fp64_switch_iter = -1;
+    if (num_lps == 0) {
+        CU(cudaStreamSynchronize(s));
+        return LPB_OK;
+    }
+    const int ce = h->opt.check_every;
+    if (h->opt.profile && (int)h->events.size() < 3 * ce + 3) {
+        for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+        h->events.assign(3 * ce + 3, nullptr);
+        for (auto& e : h->events) CU(cudaEventCreate(&e));
+    }
+    IterData<T> id = iter_data<T>(h);
+    IterBufs<T> ib = iter_bufs<T>(h);
+    CheckData cd = check_data(h, tol);
+    CU(launch_init<T>(cd, id, ib, ld, num_lps, specs_dev, wx, wy, h->c_norm_base, h->b_norm, h->rec, h->ctl, s));
+    prof.kernels += 3;
+    CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * num_lps, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h->ctl_h->error) {
+        const int code = h->ctl_h->error;
+        return fail((lpb_err)code, code == LPB_ERR_BAD_INDEX ? "an override names a variable outside [0, n)"
+                                                              : "an override record has an invalid kind or value");
+    }
+    SolveState st;
+    st.colmap.resize(num_lps);
+    for (int j = 0; j < num_lps; ++j) st.colmap[j] = j;
+    st.ncol = num_lps;
+    std::vector<int> fin;
+    for (int j = 0; j < num_lps; ++j)
+        if (h->rec_h[j].status >= 0) {
+            set_result(bt->res[j], h->rec_h[j], h->rec_h[j].status, 0, 0);
+            fin.push_back(j);
+        }
+    if ((rc = compact<T>(h, st, fin, prof)) != LPB_OK) return rc;
+    if ((rc = run_phase<T>(h, st, tol, max_iter, bt)) != LPB_OK) return rc;
+    if (!st.done) {
+        // FP64 polish: the remaining batch continues from its FP32 state with
+        // FP64 iterates; the batch state on the device (k, r0, w, ...) carries over
+        CU(launch_promote(cd, iter_bufs<float>(h), iter_bufs<double>(h), iter_data<double>(h).col, ld, st.ncol, s));
+        prof.kernels += 5;
+        prof.fp64_switch_iter = st.K;
+        if ((rc = run_phase<double>(h, st, tol, max_iter, bt)) != LPB_OK) return rc;
     }
     CU(cudaStreamSynchronize(s));
     return LPB_OK;
@@ -452,6 +530,8 @@ void lpb_default_options(lpb_options* o) {
     o->profile = 0;
     o->cuda_stream = nullptr;
     o->device = -1;
+    o->fp64_polish = 1;
+    o->polish_stall_checks = 32;
 }
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
@@ -469,7 +549,7 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
     lpb_default_options(&o);
     if (opt) o = *opt;
     if (o.precision != LPB_FP64 && o.precision != LPB_MIXED) return fail(LPB_ERR_INVALID_ARG, "bad precision");
-    if (o.check_every < 1 || o.ruiz_iters < 0 || o.power_max_iter < 1 || !(o.power_tol >= 0.0) ||
+    if (o.check_every < 1 || o.ruiz_iters < 0 || o.power_max_iter < 1 || (o.fp64_polish && o.polish_stall_checks < 1) || !(o.power_tol >= 0.0) ||
         !(o.theta >= 0.0 && o.theta <= 1.0) || !(o.beta_s >= 0.0) || !(o.beta_n >= 0.0) || !(o.beta_a >= 0.0))
         return fail(LPB_ERR_INVALID_ARG, "bad option value");
     // host validation, O(nnz)
@@ -598,6 +678,24 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
             CU(convert_f32(h->xus, h->xus32, n, s));
             CU(convert_f32(h->ls, h->ls32, m, s));
             CU(convert_f32(h->us, h->us32, m, s));
+            // double-float data of the FP32-iterate checks
+            CU(dmalloc(F, &h->A.v32lo, sizeof(float) * nnz));
+            CU(dmalloc(F, &h->At.v32lo, sizeof(float) * nnz));
+            CU(split_lo(h->A.v64, h->A.v32, h->A.v32lo, (int)nnz, s));
+            CU(split_lo(h->At.v64, h->At.v32, h->At.v32lo, (int)nnz, s));
+            df** nv[] = {&h->f_dc, &h->f_idc, &h->f_c, &h->f_xl, &h->f_xu};
+            for (df** p : nv) CU(dmalloc(F, p, sizeof(df) * n));
+            df** mv[] = {&h->f_dr, &h->f_idr, &h->f_l, &h->f_u};
+            for (df** p : mv) CU(dmalloc(F, p, sizeof(df) * mm));
+            CU(split_df(h->d_c, h->f_dc, n, false, s));
+            CU(split_df(h->d_c, h->f_idc, n, true, s));
+            CU(split_df(h->c, h->f_c, n, false, s));
+            CU(split_df(h->xl, h->f_xl, n, false, s));
+            CU(split_df(h->xu, h->f_xu, n, false, s));
+            CU(split_df(h->d_r, h->f_dr, m, false, s));
+            CU(split_df(h->d_r, h->f_idr, m, true, s));
+            CU(split_df(h->l, h->f_l, m, false, s));
+            CU(split_df(h->u, h->f_u, m, false, s));
         }
         // ||c~||, ||b~|| (w0) and the power iteration (eta)
         double* scal = nullptr;

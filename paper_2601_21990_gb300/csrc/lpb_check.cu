@@ -296,6 +296,20 @@ __global__ void k_colsum(const double* __restrict__ part, int nb_m, int nb_n, in
     if (threadIdx.y == 0 && j < ncol) colsum[(size_t)s * ld + j] = sh[0][threadIdx.x];
 }
 
+// Halpern weights (k+1)/(k+2) and 1/(k+2) of Eq. mainiter for the
+// iterations k0 .. k0+ce-1 of the next interval, computed once in FP64 so
+// that the iteration kernels do no division.
+__device__ __forceinline__ void write_halpern(double* hal64, float* hal32, int k0, int ce) {
+    for (int t = threadIdx.x; t < ce; t += blockDim.x) {
+        const double k = (double)k0 + t;
+        const double ca = (k + 1.0) / (k + 2.0), cb = 1.0 / (k + 2.0);
+        hal64[2 * t] = ca;
+        hal64[2 * t + 1] = cb;
+        hal32[2 * t] = (float)ca;
+        hal32[2 * t + 1] = (float)cb;
+    }
+}
+
 template <typename T>
 struct DecideArgs {
     const double* colsum;
@@ -303,10 +317,13 @@ struct DecideArgs {
     ColCheck col;
     ColParams<T> colp;
     double eta, tol, eps_inf, mnorm_sign, beta_s, beta_n, beta_a, theta;
-    int detect_inf, interval_len, final_check;
+    int detect_inf, interval_len, final_check, stall_checks;
     long long k_eval_global;
     ColRecord* rec;
     Control* ctl;
+    double* hal64;
+    float* hal32;
+    int check_every;
 };
 
 constexpr int kDecideThreads = 1024;
@@ -317,9 +334,10 @@ template <typename T>
 __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a) {
     __shared__ double sh_sum[kDecideThreads / 32];
     __shared__ int sh_cnt[kDecideThreads / 32];
+    __shared__ int sh_stall[kDecideThreads / 32];
     __shared__ int sh_restart;
     double lsum = 0.0;
-    int lcnt = 0;
+    int lcnt = 0, lstall = 0;
     const size_t ld = (size_t)a.ld;
     for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
         double st[kNumStats];
@@ -358,27 +376,41 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         if (status < 0) {
             lsum += r;
             ++lcnt;
+            if (a.stall_checks > 0) {
+                // an LP stalls when its KKT error has not halved for stall_checks checks
+                const double err = fmax(rel_p, fmax(rel_d, rel_g));
+                if (err < 0.5 * a.col.best[j]) {
+                    a.col.best[j] = err;
+                    a.col.stall[j] = 0;
+                } else if (++a.col.stall[j] >= a.stall_checks) {
+                    lstall = 1;
+                }
+            }
         }
     }
     // deterministic block sum
     for (int o = 16; o > 0; o >>= 1) {
         lsum += __shfl_down_sync(kFull, lsum, o);
         lcnt += __shfl_down_sync(kFull, lcnt, o);
+        lstall |= __shfl_down_sync(kFull, lstall, o);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         sh_sum[warp] = lsum;
         sh_cnt[warp] = lcnt;
+        sh_stall[warp] = lstall;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        int cnt = 0;
+        int cnt = 0, stall = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
             tot += sh_sum[q];
             cnt += sh_cnt[q];
+            stall |= sh_stall[q];
         }
         Control* c = a.ctl;
+        c->stalled = stall;
         int restart = 0;
         double rt = cnt > 0 ? tot / cnt : 0.0;
         if (cnt > 0 && !a.final_check) {
@@ -404,6 +436,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         sh_restart = restart;
     }
     __syncthreads();
+    write_halpern(a.hal64, a.hal32, a.ctl->k, a.check_every);
     if (!sh_restart) return;
     for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
         if (a.rec[j].status >= 0) continue;
@@ -455,15 +488,18 @@ struct InitArgs {
 };
 
 // runs before k_init_columns, whose blocks may raise ctl->error
-__global__ void k_init_control(Control* ctl) {
-    ctl->k = 0;
-    ctl->restart = 0;
-    ctl->error = 0;
-    ctl->pad = 0;
-    ctl->r0 = -1.0;
-    ctl->r_prev = -1.0;
-    ctl->r_avg = 0.0;
-    ctl->restarts = 0;
+__global__ void k_init_control(Control* ctl, double* hal64, float* hal32, int ce) {
+    if (threadIdx.x == 0) {
+        ctl->k = 0;
+        ctl->restart = 0;
+        ctl->error = 0;
+        ctl->stalled = 0;
+        ctl->r0 = -1.0;
+        ctl->r_prev = -1.0;
+        ctl->r_avg = 0.0;
+        ctl->restarts = 0;
+    }
+    write_halpern(hal64, hal32, 0, ce);
 }
 
 template <typename T>
@@ -519,6 +555,8 @@ __global__ void k_init_columns(const InitArgs<T> a) {
     a.colc.c[j] = oc;
     a.colc.w[j] = w;
     a.colc.lp[j] = j;
+    a.colc.best[j] = INFINITY;
+    a.colc.stall[j] = 0;
     if (j < a.ncol) {
         ColRecord rc;
         rc.status = status;
@@ -619,6 +657,8 @@ __global__ void k_compact_cols(ColParams<T> cp, ColCheck cc, const int* __restri
     cc.c[d] = cc.c[s];
     cc.w[d] = cc.w[s];
     cc.lp[d] = cc.lp[s];
+    cc.best[d] = cc.best[s];
+    cc.stall[d] = cc.stall[s];
 }
 
 inline int blocks_for(size_t work, int threads, int cap = 8192) {
@@ -626,6 +666,218 @@ inline int blocks_for(size_t work, int threads, int cap = 8192) {
     if (g < 1) g = 1;
     if (g > (size_t)cap) g = cap;
     return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// double-float checks for FP32 iterates.  The FP64 versions above run for
+// FP64 iterates; these give FP64-level accuracy on the FP32 pipe.
+// ---------------------------------------------------------------------------
+struct SpmmDfArgs {
+    int rows;
+    const int* rp;
+    const int* ci;
+    const float* vhi;   // A~ in double-float: vhi + vlo
+    const float* vlo;
+    const int* long_rows;
+    int n_long;
+    const float* s0;
+    const float* s1;
+    const float* s2;
+    df* o0;
+    df* o1;
+    df* o2;
+    int ld, ncol;
+};
+
+// o_q = A~ s_q for NOPS operands, each product a_e * x accumulated exactly
+template <int G, int NOPS>
+__global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs a) {
+    constexpr int V = 4, GPB = kBlock / G, TN = G * V;
+    __shared__ df red[NOPS * kBlock * V];
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int col0 = blockIdx.y * TN + lane * V;
+    const bool active = col0 < a.ncol;
+    const bool is_long = (int)blockIdx.x < a.n_long;
+    int row, slot = 0, nslot = 1;
+    if (is_long) {
+        row = a.long_rows[blockIdx.x];
+        slot = grp;
+        nslot = GPB;
+    } else {
+        row = ((int)blockIdx.x - a.n_long) * GPB + grp;
+        if (row >= a.rows) return;
+        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+    }
+    df acc[NOPS][V];
+#pragma unroll
+    for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[q][v] = df_zero();
+    const float* src[3] = {a.s0, a.s1, a.s2};
+    if (active) {
+        const int end = a.rp[row + 1];
+        for (int e = a.rp[row] + slot; e < end; e += nslot) {
+            const int c = a.ci[e];
+            const df w = df{a.vhi[e], a.vlo[e]};
+#pragma unroll
+            for (int q = 0; q < NOPS; ++q) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(src[q] + (size_t)c * a.ld + col0));
+                df_fma_acc(acc[q][0], w, x.x);
+                df_fma_acc(acc[q][1], w, x.y);
+                df_fma_acc(acc[q][2], w, x.z);
+                df_fma_acc(acc[q][3], w, x.w);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[q][v] = quick_two_sum(acc[q][v].hi, acc[q][v].lo);
+    if (is_long) {
+#pragma unroll
+        for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) red[(q * kBlock + threadIdx.x) * V + v] = acc[q][v];
+        __syncthreads();
+        if (grp != 0) return;
+        for (int g = 1; g < GPB; ++g)
+#pragma unroll
+            for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[q][v] = df_add(acc[q][v], red[(q * kBlock + g * G + lane) * V + v]);
+    }
+    if (!active) return;
+    const size_t off = (size_t)row * a.ld + col0;
+    df* out[3] = {a.o0, a.o1, a.o2};
+#pragma unroll
+    for (int q = 0; q < NOPS; ++q) {
+        float4* p = reinterpret_cast<float4*>(out[q] + off);
+        p[0] = make_float4(acc[q][0].hi, acc[q][0].lo, acc[q][1].hi, acc[q][1].lo);
+        p[1] = make_float4(acc[q][2].hi, acc[q][2].lo, acc[q][3].hi, acc[q][3].lo);
+    }
+}
+
+template <int NOPS>
+cudaError_t spmm_df(const Csr& m, const float* s0, const float* s1, const float* s2, df* o0, df* o1, df* o2, int ld,
+                    int ncol, cudaStream_t s) {
+    if (m.rows == 0 || ncol == 0) return cudaSuccess;
+    SpmmDfArgs a{m.rows, m.rp, m.ci, m.v32, m.v32lo, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
+    const int vecs = (ncol + 3) / 4;
+    const int G = vecs <= 1 ? 1 : vecs <= 2 ? 2 : vecs <= 4 ? 4 : vecs <= 8 ? 8 : vecs <= 16 ? 16 : 32;
+    const int gpb = kBlock / G, tn = G * 4;
+    dim3 grid(a.n_long + (a.rows + gpb - 1) / gpb, (ncol + tn - 1) / tn);
+    switch (G) {
+        case 1: k_spmm_df<1, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 2: k_spmm_df<2, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 4: k_spmm_df<4, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 8: k_spmm_df<8, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 16: k_spmm_df<16, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_spmm_df<32, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float proj_recession_f(float v, float a, float b) {
+    const bool li = isinf(a), hi = isinf(b);
+    if (li && hi) return v;
+    if (hi) return v > 0.0f ? v : 0.0f;
+    if (li) return v < 0.0f ? v : 0.0f;
+    return 0.0f;
+}
+
+__device__ __forceinline__ df df_from(double v) {
+    const float hi = (float)v;
+    return df{hi, isfinite(v) && isfinite(hi) ? (float)(v - (double)hi) : 0.0f};
+}
+
+struct ReduceDfArgs {
+    int m, n, ld, ncol;
+    const df *dr, *dc, *idr, *idc, *c, *xl, *xu, *l, *u;
+    ColCheck col;
+    const float *Xh, *DX, *X0, *X, *Yh, *DY, *DYp, *Y0, *Y;
+    const df *P0, *P1, *Q0, *Q1, *Q2;
+    double* part;
+    int restart_to_output;
+};
+
+// m-side statistics (the same quantities as k_reduce_rows_m); the terms that
+// cancel (A x against its bounds, phi sums) in double-float, norms in FP32
+__global__ void k_reduce_m_df(const ReduceDfArgs a) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const bool ok = j < a.ncol;
+    float f_pres2 = 0.f, f_ax2 = 0.f, f_dy2 = 0.f, f_cross = 0.f, f_dy02 = 0.f, f_ra2 = 0.f;
+    df d_phy = df_zero(), d_phidy = df_zero();
+    if (ok) {
+        for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.m; i += gridDim.x * kReduceRows) {
+            const size_t off = (size_t)i * a.ld + j;
+            const df dr = a.dr[i], idr = a.idr[i], l = a.l[i], u = a.u[i];
+            const df ax = df_mul(a.P0[off], idr);                    // A x, x = D_c x~
+            const float pv = df_f(df_sub(ax, df_clamp(ax, l, u)));
+            f_pres2 += pv * pv;
+            f_ax2 += ax.hi * ax.hi;
+            const float yh = a.Yh[off];
+            df_acc(d_phy, df_support(df_mulf(dr, yh), l, u));         // phi_[l,u](y), y = D_r y~
+            const float dy = a.DY[off];
+            f_dy2 += dy * dy;
+            const float p1 = df_f(a.P1[off]);
+            f_cross += dy * p1;                                      // <dy~, A~ dx~>
+            const float anchor = a.restart_to_output ? yh : a.Y[off];
+            const float dy0 = anchor - a.Y0[off];
+            f_dy02 += dy0 * dy0;
+            df_acc(d_phidy, df_support(df_mulf(dr, a.DYp[off]), l, u));
+            const float adx = df_f(df_mulf(idr, p1));                // A dx, dx = D_c dx~
+            const float t = adx - proj_recession_f(adx, l.hi, u.hi);
+            f_ra2 += t * t;
+        }
+    }
+    double s[8] = {f_pres2, f_ax2, df_d(d_phy), f_dy2, f_cross, f_dy02, df_d(d_phidy), f_ra2};
+    write_partials<8>(s, a.part, S_PRES2, kReduceBlocks, a.ld, j, ok);
+}
+
+__global__ void k_reduce_n_df(const ReduceDfArgs a) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const bool ok = j < a.ncol;
+    float f_dres2 = 0.f, f_c2 = 0.f, f_dx2 = 0.f, f_dx02 = 0.f, f_res2 = 0.f, f_rx2 = 0.f;
+    df d_ctx = df_zero(), d_phr = df_zero(), d_phidr = df_zero(), d_cdx = df_zero();
+    if (ok) {
+        const int kind = a.col.kind[j], var = a.col.var[j];
+        const df olo = df_from(a.col.lo[j]), ohi = df_from(a.col.hi[j]), oc = df_from(a.col.c[j]);
+        for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.n; i += gridDim.x * kReduceRows) {
+            const size_t off = (size_t)i * a.ld + j;
+            const df dc = a.dc[i], idc = a.idc[i];
+            df cj = a.c[i], lo = a.xl[i], hi = a.xu[i];
+            if (kind == 2) cj = var == i ? oc : df_zero();
+            else if (kind == 1 && var == i) { lo = olo; hi = ohi; }
+            const float xh = a.Xh[off];
+            const df x = df_clamp(df_mulf(dc, xh), lo, hi);
+            const df q = df_add(cj, df_mul(a.Q0[off], idc));         // c + A^T y
+            const df r = df_barrier(df_neg(q), lo, hi);              // reduced cost
+            const float d = df_f(df_add(q, r));
+            f_dres2 += d * d;
+            f_c2 += cj.hi * cj.hi;
+            df_acc(d_ctx, df_mul(cj, x));
+            df_acc(d_phr, df_support(r, lo, hi));
+            const float dx = a.DX[off];
+            f_dx2 += dx * dx;
+            const float anchor = a.restart_to_output ? xh : a.X[off];
+            const float dx0 = anchor - a.X0[off];
+            f_dx02 += dx0 * dx0;
+            // A^T y^k = A^T y^ - A^T (y^ - y^k)
+            const df gk = df_mul(df_sub(a.Q0[off], a.Q2[off]), idc);
+            const df rk = df_barrier(df_neg(df_add(cj, gk)), lo, hi);
+            const df drr = df_barrier(df_sub(r, rk), lo, hi);
+            df_acc(d_phidr, df_support(drr, lo, hi));
+            const float t = df_f(df_add(df_mul(a.Q1[off], idc), drr)); // A^T dy + dr
+            f_res2 += t * t;
+            const df dxo = df_mulf(dc, dx);
+            df_acc(d_cdx, df_mul(cj, dxo));
+            const float dxf = df_f(dxo);
+            const float t2 = dxf - proj_recession_f(dxf, lo.hi, hi.hi);
+            f_rx2 += t2 * t2;
+        }
+    }
+    double s[10] = {f_dres2, f_c2, df_d(d_ctx), df_d(d_phr), f_dx2, f_dx02, df_d(d_phidr), f_res2, df_d(d_cdx), f_rx2};
+    write_partials<10>(s, a.part, S_DRES2, kReduceBlocks, a.ld, j, ok);
 }
 
 }  // namespace
@@ -641,10 +893,21 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     double* Q0 = Q;
     double* Q1 = Q + (size_t)n * ld;
     double* Q2 = Q + 2 * (size_t)n * ld;
+    constexpr bool kDf = sizeof(T) == sizeof(float);
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    // A~ [x^, x^ - x] and A~^T [y^, Pi_B(y^ - y), y^ - y] in FP64
-    if ((e = spmm64<T, 2>(d.A, b.Xh, b.DX, nullptr, P0, P1, nullptr, ld, ncol, s)) != cudaSuccess) return e;
-    if ((e = spmm64<T, 3>(d.At, b.Yh, b.DYp, b.DY, Q0, Q1, Q2, ld, ncol, s)) != cudaSuccess) return e;
+    // A~ [x^, x^ - x] and A~^T [y^, Pi_B(y^ - y), y^ - y]: in double-float for
+    // FP32 iterates, in FP64 for FP64 iterates (P and Q hold either)
+    if constexpr (kDf) {
+        if ((e = spmm_df<2>(d.A, (const float*)b.Xh, (const float*)b.DX, nullptr, (df*)P0, (df*)P1, nullptr, ld,
+                            ncol, s)) != cudaSuccess)
+            return e;
+        if ((e = spmm_df<3>(d.At, (const float*)b.Yh, (const float*)b.DYp, (const float*)b.DY, (df*)Q0, (df*)Q1,
+                            (df*)Q2, ld, ncol, s)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = spmm64<T, 2>(d.A, b.Xh, b.DX, nullptr, P0, P1, nullptr, ld, ncol, s)) != cudaSuccess) return e;
+        if ((e = spmm64<T, 3>(d.At, b.Yh, b.DYp, b.DY, Q0, Q1, Q2, ld, ncol, s)) != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
 
     const int tiles = (ncol + 31) / 32;
@@ -683,12 +946,52 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     ra.part = partials;
     ra.restart_to_output = d.restart_to_output;
     const dim3 rblock(32, kReduceRows);
-    if (nb_m > 0) {
-        k_reduce_rows_m<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(ra);
+    if constexpr (kDf) {
+        ReduceDfArgs rd{};
+        rd.m = m;
+        rd.n = n;
+        rd.ld = ld;
+        rd.ncol = ncol;
+        rd.dr = d.f_dr;
+        rd.dc = d.f_dc;
+        rd.idr = d.f_idr;
+        rd.idc = d.f_idc;
+        rd.c = d.f_c;
+        rd.xl = d.f_xl;
+        rd.xu = d.f_xu;
+        rd.l = d.f_l;
+        rd.u = d.f_u;
+        rd.col = d.col;
+        rd.Xh = (const float*)b.Xh;
+        rd.DX = (const float*)b.DX;
+        rd.X0 = (const float*)b.X0;
+        rd.X = (const float*)b.X;
+        rd.Yh = (const float*)b.Yh;
+        rd.DY = (const float*)b.DY;
+        rd.DYp = (const float*)b.DYp;
+        rd.Y0 = (const float*)b.Y0;
+        rd.Y = (const float*)b.Y;
+        rd.P0 = (const df*)P0;
+        rd.P1 = (const df*)P1;
+        rd.Q0 = (const df*)Q0;
+        rd.Q1 = (const df*)Q1;
+        rd.Q2 = (const df*)Q2;
+        rd.part = partials;
+        rd.restart_to_output = d.restart_to_output;
+        if (nb_m > 0) {
+            k_reduce_m_df<<<dim3(nb_m, tiles), rblock, 0, s>>>(rd);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        k_reduce_n_df<<<dim3(nb_n, tiles), rblock, 0, s>>>(rd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        if (nb_m > 0) {
+            k_reduce_rows_m<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(ra);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        k_reduce_rows_n<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(ra);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_reduce_rows_n<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(ra);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_colsum<<<dim3(tiles, kNumStats), dim3(32, 32), 0, s>>>(partials, nb_m, nb_n, ld, ncol, colsum);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -707,11 +1010,15 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     da.beta_a = d.beta_a;
     da.theta = d.theta;
     da.detect_inf = d.detect_inf;
+    da.stall_checks = d.stall_checks;
     da.interval_len = interval_len;
     da.final_check = final_check ? 1 : 0;
     da.k_eval_global = (long long)k_eval_global;
     da.rec = rec;
     da.ctl = ctl;
+    da.hal64 = d.hal64;
+    da.hal32 = d.hal32;
+    da.check_every = d.check_every;
     k_decide<T><<<1, kDecideThreads, 0, s>>>(da);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_restart_copy<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.X0, b.Xh, n, ld, ncol,
@@ -747,7 +1054,7 @@ cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBuf
     a.colc = d.col;
     a.rec = rec;
     a.ctl = ctl;
-    k_init_control<<<1, 1, 0, s>>>(ctl);
+    k_init_control<<<1, 256, 0, s>>>(ctl, d.hal64, d.hal32, d.check_every);
     k_init_columns<T><<<(ld + 255) / 256, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -778,7 +1085,52 @@ cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int
     return cudaGetLastError();
 }
 
-#define LPB_INSTANTIATE(T)                                                                                           \
+namespace {
+
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, int rows, int ld, int ncol) {
+    const size_t total = (size_t)rows * ld;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
+        if ((int)(p % ld) < ncol) dst[p] = (double)src[p];
+}
+
+// FP64 per-column parameters from the FP64 originals: the same formulas as
+// k_init_columns, with the current primal weight
+__global__ void k_colparams64(ColCheck cc, ColParams<double> cp, const double* __restrict__ d_c, double eta,
+                              int ld) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ld) return;
+    const int kind = cc.kind[j], var = cc.var[j];
+    double lo = 0.0, hi = 0.0, c = 0.0;
+    if (kind == 1) {
+        lo = cc.lo[j] / d_c[var];
+        hi = cc.hi[j] / d_c[var];
+    } else if (kind == 2) {
+        c = d_c[var] * cc.c[j];
+    }
+    cp.lo[j] = lo;
+    cp.hi[j] = hi;
+    cp.c[j] = c;
+    cp.tau[j] = eta / cc.w[j];
+    cp.sigma[j] = eta * cc.w[j];
+    cc.stall[j] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_promote(const CheckData& d, const IterBufs<float>& src, const IterBufs<double>& dst,
+                           ColParams<double> colp64, int ld, int ncol, cudaStream_t s) {
+    const int n = d.n, m = d.m;
+    k_widen<<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(src.X, dst.X, n, ld, ncol);
+    k_widen<<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(src.X0, dst.X0, n, ld, ncol);
+    if (m > 0) {
+        k_widen<<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(src.Y, dst.Y, m, ld, ncol);
+        k_widen<<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(src.Y0, dst.Y0, m, ld, ncol);
+    }
+    k_colparams64<<<(ld + 255) / 256, 256, 0, s>>>(d.col, colp64, d.d_c, d.eta, ld);
+    return cudaGetLastError();
+}
+
+#define LPB_INSTANTIATE(T)                                                                                        \
     template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int64_t, int, bool, double*, \
                                          double*, double*, double*, ColRecord*, Control*, ColParams<T>, cudaStream_t, \
                                          cudaEvent_t*);                                                               \

@@ -14,11 +14,12 @@
 #include <stdint.h>
 
 #include "lpb.h"
+#include "lpb_df.h"
 
 namespace lpb {
 
 constexpr int kBlock = 256;        // threads of every iteration / SpMM block
-constexpr int kLongRow = 128;      // rows with more nonzeros get a whole block
+constexpr int kLongRow = 64;       // rows with more nonzeros get a whole block
 constexpr int kReduceRows = 8;     // rows per step of a reduction block (blockDim.y)
 constexpr int kReduceBlocks = 304; // reduction blocks per column tile (2 per SM)
 constexpr int kNumStats = 18;      // per-column partial sums of a check
@@ -53,6 +54,7 @@ struct Csr {
     int* ci = nullptr;          // nnz
     double* v64 = nullptr;      // scaled values, FP64
     float* v32 = nullptr;       // scaled values, FP32 (mixed path)
+    float* v32lo = nullptr;     // v64 - v32 rounded to FP32: (v32, v32lo) is v64 in double-float
     int* long_rows = nullptr;   // rows with > kLongRow entries
     int n_long = 0;
 };
@@ -79,6 +81,8 @@ struct ColCheck {
     double* c;    // kind 2: sign
     double* w;    // primal weight
     int* lp;      // LP index of the column in the caller's batch
+    double* best; // smallest KKT error seen since the last halving (stall test)
+    int* stall;   // checks since the KKT error last halved
 };
 
 // One column's outcome of a check, copied to the host.
@@ -94,7 +98,7 @@ struct Control {
     int k;          // inner index of the first iteration of the next interval
     int restart;    // 1 if the last check restarted
     int error;      // device-side check flags (LPB_ERR_*)
-    int pad;
+    int stalled;    // 1 if an active LP stalled at the last check
     double r0;      // residual at the start of the epoch (< 0: unset)
     double r_prev;  // residual at the previous check
     double r_avg;   // averaged residual of the last check
@@ -120,6 +124,10 @@ cudaError_t scale_vectors(int m, int n, const double* d_r, const double* d_c, co
 cudaError_t sq_norm(const double* v, int count, double* out_dev, cudaStream_t s);
 cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev, cudaStream_t s);
 cudaError_t convert_f32(const double* in, float* out, int count, cudaStream_t s);
+// out[i] = in[i] (or 1 / in[i] when recip) as a double-float pair
+cudaError_t split_df(const double* in, df* out, int count, bool recip, cudaStream_t s);
+// lo[e] = v64[e] - (double)v32[e] rounded to FP32
+cudaError_t split_lo(const double* v64, const float* v32, float* lo, int count, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // iteration (lpb_iter.cu)
@@ -143,10 +151,11 @@ struct IterData {
 // One reflected-Halpern PDHG iteration on columns [0, ncol): primal step
 // (A~^T Y fused with the box projection, reflection and Halpern update) then
 // dual step (A~ Xbar fused with the row projection and Halpern update).
-// k_dev[0] + t is the inner index k of Eq. mainiter.
+// hal[2t], hal[2t+1] are the Halpern weights (k+1)/(k+2), 1/(k+2) of
+// Eq. mainiter for iteration t of the interval, written on the device.
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol,
-                             const int* k_dev, int t, bool check, cudaStream_t s,
+                             const T* hal, int t, bool check, cudaStream_t s,
                              cudaEvent_t* ev /* 3 events or nullptr */);
 
 // ---------------------------------------------------------------------------
@@ -161,6 +170,13 @@ struct CheckData {
     ColCheck col;
     double eta, beta_s, beta_n, beta_a, theta, mnorm_sign, eps_inf, tol;
     int detect_inf, restart_to_output;
+    int stall_checks;              // 0: no stall test
+    int check_every;
+    double* hal64;                 // Halpern weights of the next interval (2 * check_every)
+    float* hal32;
+    // double-float copies for the FP32-iterate checks: scalings, their
+    // reciprocals, original c, xlo, xhi (n) and l, u (m)
+    const df *f_dr, *f_dc, *f_idr, *f_idc, *f_c, *f_xl, *f_xu, *f_l, *f_u;
 };
 
 template <typename T>
@@ -178,6 +194,11 @@ template <typename T>
 cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev,
                            const int* lps_dev, int count, const double* xl_base, const double* xu_base,
                            double* x_out, double* y_out, cudaStream_t s);
+
+// FP64 polish: widens the FP32 state (X, X0, Y, Y0) of the active batch to
+// FP64 and fills the FP64 per-column parameters from the FP64 originals.
+cudaError_t launch_promote(const CheckData& d, const IterBufs<float>& src, const IterBufs<double>& dst,
+                           ColParams<double> colp64, int ld, int ncol, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int* src_dev, const int* dst_dev,

@@ -20,6 +20,13 @@
 // never touch memory.  Per-LP overrides (Sec. 5.1, 5.2) are applied by
 // comparing the row index with each column's override variable; the
 // matrices X_lo, X_hi and C are never formed.
+//
+// The per-column parameters of the block's column tile are staged in shared
+// memory once per block, and the row's own operands (iterate, anchor, bounds)
+// are loaded before the gather loop so that their latency overlaps it.  No
+// FP64 instruction runs in the FP32 kernels (GB300 executes FP64 at a small
+// fraction of its FP32 rate); the Halpern weights come from a table written
+// by the check kernels.
 #include "lpb_internal.h"
 
 namespace lpb {
@@ -52,23 +59,14 @@ __device__ __forceinline__ void stv(float* p, const float (&r)[4]) {
 __device__ __forceinline__ void stv(double* p, const double (&r)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
 }
-__device__ __forceinline__ void ldv_i(const int* p, int (&r)[4]) {
-    int4 u = *reinterpret_cast<const int4*>(p);
-    r[0] = u.x; r[1] = u.y; r[2] = u.z; r[3] = u.w;
-}
-__device__ __forceinline__ void ldv_i(const int* p, int (&r)[2]) {
-    int2 u = *reinterpret_cast<const int2*>(p);
-    r[0] = u.x; r[1] = u.y;
-}
 
 // acc += sum over the row's nonzeros e = beg+slot, beg+slot+nslot, ... of
 // a_e * src[col_e, col0 .. col0+V)
 template <typename T, int V>
-__device__ __forceinline__ void gather_row(const int* __restrict__ rp, const int* __restrict__ ci,
-                                           const T* __restrict__ va, const T* __restrict__ src, int ld, int col0,
-                                           int row, int slot, int nslot, T (&acc)[V]) {
-    const int end = rp[row + 1];
-    int e = rp[row] + slot;
+__device__ __forceinline__ void gather_row(const int* __restrict__ ci, const T* __restrict__ va,
+                                           const T* __restrict__ src, int ld, int col0, int beg, int end, int slot,
+                                           int nslot, T (&acc)[V]) {
+    int e = beg + slot;
     for (; e + 3 * nslot < end; e += 4 * nslot) {
         const int c0 = ci[e], c1 = ci[e + nslot], c2 = ci[e + 2 * nslot], c3 = ci[e + 3 * nslot];
         const T a0 = va[e], a1 = va[e + nslot], a2 = va[e + 2 * nslot], a3 = va[e + 3 * nslot];
@@ -95,6 +93,62 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ rp, const int
     }
 }
 
+// acc += sum over the entries [beg, end) of a_e * src[col_e, col0 .. col0+V).
+// The G lanes of the row group load up to R = G*K of the row's (col, value)
+// pairs at once (K per lane, coalesced), then broadcast them by shuffle and
+// issue the gathers four at a time, so a row of up to R entries costs one
+// index round trip and a pipelined burst of gathers.
+template <typename T, int V, int G>
+__device__ __forceinline__ void gather_coop(const int* __restrict__ ci, const T* __restrict__ va,
+                                            const T* __restrict__ src, int ld, int col0, int beg, int end,
+                                            T (&acc)[V]) {
+    constexpr int K = G >= 16 ? 1 : 16 / G;
+    constexpr int R = G * K;
+    const int lane = threadIdx.x % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    for (int e0 = beg; e0 < end; e0 += R) {
+        int c[K];
+        T a[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int me = e0 + q * G + lane;
+            c[q] = me < end ? __ldg(ci + me) : 0;
+            a[q] = me < end ? __ldg(va + me) : T(0);
+        }
+        const int cnt = min(R, end - e0);
+        // entry k of the round sits in register slot k / G of lane k % G
+        // (compile-time after unrolling); entries past cnt get a = 0 and the
+        // round's first column, so every gather stays in bounds
+        const int cfirst = __shfl_sync(gmask, c[0], 0, G);
+#pragma unroll
+        for (int k0 = 0; k0 < R; k0 += 4) {
+            if (k0 >= cnt) break;
+            int cc[4];
+            T aa[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + j;
+                const int cs = __shfl_sync(gmask, c[k / G], k % G, G);
+                const T as = __shfl_sync(gmask, a[k / G], k % G, G);
+                cc[j] = k < cnt ? cs : cfirst;
+                aa[j] = k < cnt ? as : T(0);
+            }
+            T x0[V], x1[V], x2[V], x3[V];
+            ldg_v(src + (size_t)cc[0] * ld + col0, x0);
+            ldg_v(src + (size_t)cc[1] * ld + col0, x1);
+            ldg_v(src + (size_t)cc[2] * ld + col0, x2);
+            ldg_v(src + (size_t)cc[3] * ld + col0, x3);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc[v] = fma(aa[0], x0[v], acc[v]);
+                acc[v] = fma(aa[1], x1[v], acc[v]);
+                acc[v] = fma(aa[2], x2[v], acc[v]);
+                acc[v] = fma(aa[3], x3[v], acc[v]);
+            }
+        }
+    }
+}
+
 template <typename T>
 struct StepArgs {
     // sparse operator (rows of A~^T for the primal step, of A~ for the dual step)
@@ -111,15 +165,36 @@ struct StepArgs {
     T* Zbar;          // primal: Xbar out
     T* Zh;            // check: x^ / y^
     T* DZ;            // check: x^ - X^k / y^ - Y^k
-    T* Aux;           // check: G = A~^T Y^k (primal) / Pi_B(y^ - Y^k) (dual)
+    T* Aux;           // check, dual: Pi_B(y^ - Y^k)
     const T* rc;      // primal: scaled c (n)
     const T* rlo;     // scaled lower bounds of the rows (xlo or l)
     const T* rhi;
     ColParams<T> col;
     int ld, ncol;
-    const int* k_dev;
+    const T* hal;     // (k+1)/(k+2), 1/(k+2) of Eq. mainiter for each t of the interval
     int t;
 };
+
+// Row handled by this thread's row group: a long row (whole block, row
+// groups split the nonzeros) or a short one.  Returns false when the group
+// has no row.
+template <int G>
+__device__ __forceinline__ bool pick_row(const int* __restrict__ rp, const int* __restrict__ long_rows, int n_long,
+                                         int rows, int& row, int& slot, int& nslot, bool& is_long) {
+    constexpr int GPB = kBlock / G;
+    const int grp = threadIdx.x / G;
+    is_long = (int)blockIdx.x < n_long;
+    if (is_long) {
+        row = long_rows[blockIdx.x];
+        slot = grp;
+        nslot = GPB;
+        return true;
+    }
+    row = ((int)blockIdx.x - n_long) * GPB + grp;
+    slot = 0;
+    nslot = 1;
+    return row < rows && rp[row + 1] - rp[row] <= kLongRow;
+}
 
 // Reduce the row groups' partial sums of a long row through shared memory;
 // on return only row group 0 holds the sum.  Every thread of the block calls it.
@@ -139,52 +214,68 @@ __device__ __forceinline__ bool long_row_reduce(T (&acc)[V], T* red) {
 
 template <typename T, int G, bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_primal(const StepArgs<T> a) {
-    constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
+    constexpr int V = Vec<T>::V, TN = G * V;
     __shared__ T red[kBlock * V];
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int col0 = blockIdx.y * TN + lane * V;
+    __shared__ T s_tau[TN], s_lo[TN], s_hi[TN], s_c[TN];
+    __shared__ int s_kind[TN], s_var[TN];
+    const int lane = threadIdx.x % G;
+    const int tile0 = blockIdx.y * TN;
+    for (int q = threadIdx.x; q < TN; q += kBlock) {
+        const int j = tile0 + q;
+        const bool in = j < a.ld;
+        s_kind[q] = in ? a.col.kind[j] : 0;
+        s_var[q] = in ? a.col.var[j] : -1;
+        s_tau[q] = in ? a.col.tau[j] : T(0);
+        s_lo[q] = in ? a.col.lo[j] : T(0);
+        s_hi[q] = in ? a.col.hi[j] : T(0);
+        s_c[q] = in ? a.col.c[j] : T(0);
+    }
+    __syncthreads();
+    const int col0 = tile0 + lane * V;
     const bool active = col0 < a.ncol;
-    const bool is_long = (int)blockIdx.x < a.n_long;
-    int row, slot = 0, nslot = 1;
-    if (is_long) {
-        row = a.long_rows[blockIdx.x];
-        slot = grp;
-        nslot = GPB;
-    } else {
-        row = ((int)blockIdx.x - a.n_long) * GPB + grp;
-        if (row >= a.rows) return;
-        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+    int row, slot, nslot;
+    bool is_long;
+    if (!pick_row<G>(a.rp, a.long_rows, a.n_long, a.rows, row, slot, nslot, is_long)) return;
+    const bool owner = active && (!is_long || slot == 0);
+
+    // the epilogue's operands, issued before the gather
+    const size_t off = (size_t)row * a.ld + col0;
+    T x[V], x0[V], cr = T(0), lor = T(0), hir = T(0);
+    if (owner) {
+        ldv(a.Z + off, x);
+        ldv(a.Z0 + off, x0);
+        cr = a.rc[row];
+        lor = a.rlo[row];
+        hir = a.rhi[row];
     }
     T acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = T(0);
-    if (active) gather_row<T, V>(a.rp, a.ci, a.va, a.src, a.ld, col0, row, slot, nslot, acc);
+    {
+        // a long row is cut into nslot contiguous pieces, one per row group;
+        // every lane of a group takes part in its shuffles, so lanes past the
+        // last column gather the tile's first (valid) column and drop the sum
+        int beg = a.rp[row], end = a.rp[row + 1];
+        if (nslot > 1) {
+            const int piece = (end - beg + nslot - 1) / nslot;
+            beg = min(end, beg + slot * piece);
+            end = min(end, beg + piece);
+        }
+        gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
+    }
     if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
     if (!active) return;
 
-    int kind[V], var[V];
-    T tau[V], olo[V], ohi[V], oc[V];
-    ldv_i(a.col.kind + col0, kind);
-    ldv_i(a.col.var + col0, var);
-    ldv(a.col.tau + col0, tau);
-    ldv(a.col.lo + col0, olo);
-    ldv(a.col.hi + col0, ohi);
-    ldv(a.col.c + col0, oc);
-    const int k = *a.k_dev + a.t;
-    const T ca = (T)((double)(k + 1) / (double)(k + 2));
-    const T cb = (T)(1.0 / (double)(k + 2));
-
-    const size_t off = (size_t)row * a.ld + col0;
-    T x[V], x0[V], xh[V], xb[V], xn[V], dz[V];
-    ldv(a.Z + off, x);
-    ldv(a.Z0 + off, x0);
-    const T cr = a.rc[row], lor = a.rlo[row], hir = a.rhi[row];
+    const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
+    T xh[V], xb[V], xn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
+        const int q = lane * V + v;
+        const int kind = s_kind[q], var = s_var[q];
         T cj = cr, lo = lor, hi = hir;
-        if (kind[v] == 2) cj = var[v] == row ? oc[v] : T(0);
-        else if (kind[v] == 1 && var[v] == row) { lo = olo[v]; hi = ohi[v]; }
-        const T step = tau[v] * (cj + acc[v]);
+        if (kind == 2) cj = var == row ? s_c[q] : T(0);
+        else if (kind == 1 && var == row) { lo = s_lo[q]; hi = s_hi[q]; }
+        const T step = s_tau[q] * (cj + acc[v]);
         T s = x[v] - step;
         const bool inside = s < hi && s > lo;
         s = s < hi ? s : hi;
@@ -216,50 +307,62 @@ __device__ __forceinline__ T barrier(T v, T lo, T hi) {
 
 template <typename T, int G, bool CHECK>
 __global__ void __launch_bounds__(kBlock) k_dual(const StepArgs<T> a) {
-    constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
+    constexpr int V = Vec<T>::V, TN = G * V;
     __shared__ T red[kBlock * V];
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int col0 = blockIdx.y * TN + lane * V;
+    __shared__ T s_sigma[TN];
+    const int lane = threadIdx.x % G;
+    const int tile0 = blockIdx.y * TN;
+    for (int q = threadIdx.x; q < TN; q += kBlock) {
+        const int j = tile0 + q;
+        s_sigma[q] = j < a.ld ? a.col.sigma[j] : T(1);
+    }
+    __syncthreads();
+    const int col0 = tile0 + lane * V;
     const bool active = col0 < a.ncol;
-    const bool is_long = (int)blockIdx.x < a.n_long;
-    int row, slot = 0, nslot = 1;
-    if (is_long) {
-        row = a.long_rows[blockIdx.x];
-        slot = grp;
-        nslot = GPB;
-    } else {
-        row = ((int)blockIdx.x - a.n_long) * GPB + grp;
-        if (row >= a.rows) return;
-        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+    int row, slot, nslot;
+    bool is_long;
+    if (!pick_row<G>(a.rp, a.long_rows, a.n_long, a.rows, row, slot, nslot, is_long)) return;
+    const bool owner = active && (!is_long || slot == 0);
+
+    const size_t off = (size_t)row * a.ld + col0;
+    T y[V], y0[V], lr = T(0), ur = T(0);
+    if (owner) {
+        ldv(a.Z + off, y);
+        ldv(a.Z0 + off, y0);
+        lr = a.rlo[row];
+        ur = a.rhi[row];
     }
     T acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = T(0);
-    if (active) gather_row<T, V>(a.rp, a.ci, a.va, a.src, a.ld, col0, row, slot, nslot, acc);
+    {
+        // a long row is cut into nslot contiguous pieces, one per row group;
+        // every lane of a group takes part in its shuffles, so lanes past the
+        // last column gather the tile's first (valid) column and drop the sum
+        int beg = a.rp[row], end = a.rp[row + 1];
+        if (nslot > 1) {
+            const int piece = (end - beg + nslot - 1) / nslot;
+            beg = min(end, beg + slot * piece);
+            end = min(end, beg + piece);
+        }
+        gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
+    }
     if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
     if (!active) return;
 
-    T sigma[V];
-    ldv(a.col.sigma + col0, sigma);
-    const int k = *a.k_dev + a.t;
-    const T ca = (T)((double)(k + 1) / (double)(k + 2));
-    const T cb = (T)(1.0 / (double)(k + 2));
-
-    const size_t off = (size_t)row * a.ld + col0;
-    T y[V], y0[V], yh[V], yn[V], dz[V];
-    ldv(a.Z + off, y);
-    ldv(a.Z0 + off, y0);
-    const T lr = a.rlo[row], ur = a.rhi[row];
+    const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
+    T yh[V], yn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const T s = y[v] / sigma[v] + acc[v];
+        const T sg = s_sigma[lane * V + v];
+        const T s = y[v] / sg + acc[v];
         T p = s < ur ? s : ur;
         p = p > lr ? p : lr;
-        yh[v] = sigma[v] * (s - p);
+        yh[v] = sg * (s - p);
         yn[v] = ca * (T(2) * yh[v] - y[v]) + cb * y0[v];
         // y^ - y: y^ = 0 exactly where the row bound is not active; where it
         // is, y^ - y = sigma (A xb - Pi(v)) without the cancellation of y
-        dz[v] = p == s ? -y[v] : sigma[v] * (acc[v] - p);
+        dz[v] = p == s ? -y[v] : sg * (acc[v] - p);
     }
     stv(a.Z + off, yn);
     if (CHECK) {
@@ -302,7 +405,7 @@ cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, cudaStr
 }  // namespace
 
 template <typename T>
-cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol, const int* k_dev, int t,
+cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol, const T* hal, int t,
                              bool check, cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
     StepArgs<T> p{};
@@ -318,14 +421,14 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.Zbar = b.Xbar;
     p.Zh = b.Xh;
     p.DZ = b.DX;
-    p.Aux = b.G;
+    p.Aux = nullptr;
     p.rc = d.c;
     p.rlo = d.xl;
     p.rhi = d.xu;
     p.col = d.col;
     p.ld = ld;
     p.ncol = ncol;
-    p.k_dev = k_dev;
+    p.hal = hal;
     p.t = t;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     if ((e = dispatch_step<T>(true, check, p, s)) != cudaSuccess) return e;
@@ -351,16 +454,16 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.col = d.col;
     q.ld = ld;
     q.ncol = ncol;
-    q.k_dev = k_dev;
+    q.hal = hal;
     q.t = t;
     if ((e = dispatch_step<T>(false, check, q, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-template cudaError_t launch_iteration<float>(const IterData<float>&, const IterBufs<float>&, int, int, const int*,
+template cudaError_t launch_iteration<float>(const IterData<float>&, const IterBufs<float>&, int, int, const float*,
                                              int, bool, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_iteration<double>(const IterData<double>&, const IterBufs<double>&, int, int,
-                                              const int*, int, bool, cudaStream_t, cudaEvent_t*);
+                                              const double*, int, bool, cudaStream_t, cudaEvent_t*);
 
 }  // namespace lpb

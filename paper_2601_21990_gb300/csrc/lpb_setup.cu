@@ -508,6 +508,35 @@ cudaError_t convert_f32(const double* in, float* out, int count, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+// hi = value rounded to FP32, lo = the rounding error rounded to FP32; an
+// infinite value is {+-inf, 0}
+__global__ void k_split_df(const double* __restrict__ in, df* __restrict__ out, int count, bool recip) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const double v = recip ? 1.0 / in[i] : in[i];
+        const float hi = (float)v;
+        out[i] = df{hi, isfinite(v) && isfinite(hi) ? (float)(v - (double)hi) : 0.0f};
+    }
+}
+__global__ void k_split_lo(const double* __restrict__ v64, const float* __restrict__ v32, float* __restrict__ lo,
+                           int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        lo[i] = (float)(v64[i] - (double)v32[i]);
+}
+}  // namespace
+
+cudaError_t split_df(const double* in, df* out, int count, bool recip, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_split_df<<<grid_for(count, 256), 256, 0, s>>>(in, out, count, recip);
+    return cudaGetLastError();
+}
+
+cudaError_t split_lo(const double* v64, const float* v32, float* lo, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_split_lo<<<grid_for(count, 256), 256, 0, s>>>(v64, v32, lo, count);
+    return cudaGetLastError();
+}
+
 static cudaError_t two_stage(const double* a, const double* b, int count, int mode, double* out_dev, double* part,
                              cudaStream_t s) {
     k_sum_stage1<<<kSumBlocks, kSumThreads, 0, s>>>(a, b, count, mode, part);

@@ -45,7 +45,7 @@ class Options(C.Structure):
                 ("restart_to_pdhg_output", C.c_int32), ("power_max_iter", C.c_int32),
                 ("power_tol", C.c_double), ("power_seed", C.c_uint64), ("eps_infeas", C.c_double),
                 ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32)]
 
 
 class Spec(C.Structure):
@@ -62,7 +62,7 @@ class Result(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("bytes", C.c_double * 4),
                 ("setup_ms", C.c_double), ("checks", C.c_int64), ("compactions", C.c_int64),
-                ("kernels", C.c_int64)]
+                ("kernels", C.c_int64), ("fp64_switch_iter", C.c_int64)]
 
 
 SPEC_DTYPE = np.dtype([("kind", "<i4"), ("var", "<i4"), ("lo", "<f8"), ("hi", "<f8"), ("sign", "<f8")])

@@ -1,0 +1,22 @@
+"""Host-side pins of the double-float arithmetic the FP32-iterate checks use
+(csrc/lpb_df.h): error-free TwoSum / TwoProd, df add / mul / FMA-accumulate
+against FP64, and the handling of infinite bounds.  Built with nvcc for the
+host; runs without a GPU."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_double_float_helpers(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "df_host_test"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2601_21990_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "native", "df_host_test.cu"), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout[-2000:]
