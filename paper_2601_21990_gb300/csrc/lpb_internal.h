@@ -18,8 +18,14 @@
 
 namespace lpb {
 
-constexpr int kBlock = 256;        // threads of every iteration / SpMM block
-constexpr int kLongRow = 64;       // rows with more nonzeros get a whole block
+#ifndef LPB_BLOCK
+#define LPB_BLOCK 128
+#endif
+#ifndef LPB_LONG_ROW
+#define LPB_LONG_ROW 32
+#endif
+constexpr int kBlock = LPB_BLOCK;     // threads of every iteration / SpMM block
+constexpr int kLongRow = LPB_LONG_ROW; // rows with more nonzeros get a whole block
 constexpr int kReduceRows = 8;     // rows per step of a reduction block (blockDim.y)
 constexpr int kReduceBlocks = 304; // reduction blocks per column tile (2 per SM)
 constexpr int kNumStats = 18;      // per-column partial sums of a check

@@ -22,12 +22,16 @@
 // matrices X_lo, X_hi and C are never formed.
 //
 // The per-column parameters of the block's column tile are staged in shared
-// memory once per block, and the row's own operands (iterate, anchor, bounds)
-// are loaded before the gather loop so that their latency overlaps it.  No
+// memory once per block.  No
 // FP64 instruction runs in the FP32 kernels (GB300 executes FP64 at a small
 // fraction of its FP32 rate); the Halpern weights come from a table written
 // by the check kernels.
 #include "lpb_internal.h"
+
+// resident blocks per SM the step kernels are compiled for (register cap)
+#ifndef LPB_STEP_MIN_BLOCKS
+#define LPB_STEP_MIN_BLOCKS 1
+#endif
 
 namespace lpb {
 
@@ -58,39 +62,6 @@ __device__ __forceinline__ void stv(float* p, const float (&r)[4]) {
 }
 __device__ __forceinline__ void stv(double* p, const double (&r)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
-}
-
-// acc += sum over the row's nonzeros e = beg+slot, beg+slot+nslot, ... of
-// a_e * src[col_e, col0 .. col0+V)
-template <typename T, int V>
-__device__ __forceinline__ void gather_row(const int* __restrict__ ci, const T* __restrict__ va,
-                                           const T* __restrict__ src, int ld, int col0, int beg, int end, int slot,
-                                           int nslot, T (&acc)[V]) {
-    int e = beg + slot;
-    for (; e + 3 * nslot < end; e += 4 * nslot) {
-        const int c0 = ci[e], c1 = ci[e + nslot], c2 = ci[e + 2 * nslot], c3 = ci[e + 3 * nslot];
-        const T a0 = va[e], a1 = va[e + nslot], a2 = va[e + 2 * nslot], a3 = va[e + 3 * nslot];
-        T x0[V], x1[V], x2[V], x3[V];
-        ldg_v(src + (size_t)c0 * ld + col0, x0);
-        ldg_v(src + (size_t)c1 * ld + col0, x1);
-        ldg_v(src + (size_t)c2 * ld + col0, x2);
-        ldg_v(src + (size_t)c3 * ld + col0, x3);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            acc[v] = fma(a0, x0[v], acc[v]);
-            acc[v] = fma(a1, x1[v], acc[v]);
-            acc[v] = fma(a2, x2[v], acc[v]);
-            acc[v] = fma(a3, x3[v], acc[v]);
-        }
-    }
-    for (; e < end; e += nslot) {
-        const int c0 = ci[e];
-        const T a0 = va[e];
-        T x0[V];
-        ldg_v(src + (size_t)c0 * ld + col0, x0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = fma(a0, x0[v], acc[v]);
-    }
 }
 
 // acc += sum over the entries [beg, end) of a_e * src[col_e, col0 .. col0+V).
@@ -213,7 +184,7 @@ __device__ __forceinline__ bool long_row_reduce(T (&acc)[V], T* red) {
 }
 
 template <typename T, int G, bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_primal(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_primal(const StepArgs<T> a) {
     constexpr int V = Vec<T>::V, TN = G * V;
     __shared__ T red[kBlock * V];
     __shared__ T s_tau[TN], s_lo[TN], s_hi[TN], s_c[TN];
@@ -241,13 +212,13 @@ __global__ void __launch_bounds__(kBlock) k_primal(const StepArgs<T> a) {
     // the epilogue's operands, issued before the gather
     const size_t off = (size_t)row * a.ld + col0;
     T x[V], x0[V], cr = T(0), lor = T(0), hir = T(0);
-    if (owner) {
+    auto load_epilogue = [&]() {
         ldv(a.Z + off, x);
         ldv(a.Z0 + off, x0);
         cr = a.rc[row];
         lor = a.rlo[row];
         hir = a.rhi[row];
-    }
+    };
     T acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = T(0);
@@ -263,6 +234,9 @@ __global__ void __launch_bounds__(kBlock) k_primal(const StepArgs<T> a) {
         }
         gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
     }
+    // the row's own operands are loaded after the gather: issuing them first
+    // keeps them live across it and costs occupancy (measured slower)
+    if (owner) load_epilogue();
     if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
     if (!active) return;
 
@@ -306,7 +280,7 @@ __device__ __forceinline__ T barrier(T v, T lo, T hi) {
 }
 
 template <typename T, int G, bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_dual(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_dual(const StepArgs<T> a) {
     constexpr int V = Vec<T>::V, TN = G * V;
     __shared__ T red[kBlock * V];
     __shared__ T s_sigma[TN];
@@ -326,12 +300,12 @@ __global__ void __launch_bounds__(kBlock) k_dual(const StepArgs<T> a) {
 
     const size_t off = (size_t)row * a.ld + col0;
     T y[V], y0[V], lr = T(0), ur = T(0);
-    if (owner) {
+    auto load_epilogue = [&]() {
         ldv(a.Z + off, y);
         ldv(a.Z0 + off, y0);
         lr = a.rlo[row];
         ur = a.rhi[row];
-    }
+    };
     T acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = T(0);
@@ -347,6 +321,9 @@ __global__ void __launch_bounds__(kBlock) k_dual(const StepArgs<T> a) {
         }
         gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
     }
+    // the row's own operands are loaded after the gather: issuing them first
+    // keeps them live across it and costs occupancy (measured slower)
+    if (owner) load_epilogue();
     if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
     if (!active) return;
 
