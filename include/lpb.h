@@ -168,6 +168,28 @@ lpb_err lpb_handle_info(lpb_handle h, double* eta, double* norm_est, int32_t* po
 /* Scaling factors D_r (m) and D_c (n) of A~ = D_r A D_c, copied to the host. */
 lpb_err lpb_scaling(lpb_handle h, double* d_row, double* d_col);
 
+/* Equilibration factors without allocating anything.  The paper has no
+ * counterpart; this serves callers that cannot call cudaMalloc: code running
+ * while a CUDA graph is being captured, latency-critical callers that must
+ * not trigger the allocator's device-wide synchronization, and hosts whose
+ * device memory is owned by their own pool allocator.  It computes the same
+ * factors as lpb_create (ruiz_iters Ruiz infinity-norm passes, then one
+ * Pock-Chambolle pass when pock_chambolle != 0; A~ = D_r A D_c) for an m x n
+ * CSR matrix already in device memory: row_ptr_dev (m+1 int32), col_idx_dev
+ * (nnz int32) and vals_dev (nnz finite doubles) are read, d_row_dev (m) and
+ * d_col_dev (n) are written; all are device pointers owned by the caller.
+ * Work is queued on cuda_stream (NULL: the default stream); the factors are
+ * valid once that stream reaches this point.  The scratch is a fixed
+ * device-resident array of 2^21 doubles in this library, held by every GPU
+ * that loads it until the process exits: m + n above 2097152 returns
+ * LPB_ERR_INVALID_ARG.  A device's first call looks up that array's address
+ * (make it before any stream capture); calls share the array, so calls that
+ * overlap on the GPU race on it.  The column sums of the last pass come from
+ * atomic updates, so they may differ from lpb_create's in the last bits. */
+lpb_err lpb_scaling_noalloc(int32_t m, int32_t n, int32_t nnz, const int32_t* row_ptr_dev,
+                            const int32_t* col_idx_dev, const double* vals_dev, int32_t ruiz_iters,
+                            int32_t pock_chambolle, double* d_row_dev, double* d_col_dev, void* cuda_stream);
+
 void lpb_batch_free(lpb_batch_t b);
 void lpb_destroy(lpb_handle h);
 

@@ -536,6 +536,12 @@ void lpb_default_options(lpb_options* o) {
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+void lpb::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+extern "C" {
+
 lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                    const double* vals, const double* c, const double* row_lo, const double* row_hi,
                    const double* var_lo, const double* var_hi, const lpb_options* opt, lpb_handle* out) {

@@ -111,6 +111,9 @@ struct Control {
     int64_t restarts;
 };
 
+// records the message lpb_last_error() returns on this thread (lpb_api.cu)
+void set_last_error(const char* msg);
+
 // ---------------------------------------------------------------------------
 // setup (lpb_setup.cu)
 // ---------------------------------------------------------------------------

@@ -29,7 +29,7 @@ FP64, MIXED = 0, 1
 # every symbol include/lpb.h declares
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
            "lpb_result_device", "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_batch_free",
-           "lpb_destroy", "lpb_last_error"]
+           "lpb_destroy", "lpb_last_error", "lpb_scaling_noalloc"]
 
 
 class LpbError(RuntimeError):
@@ -96,8 +96,9 @@ def load(path: str = LIB_PATH):
     lib.lpb_destroy.argtypes = [vp]
     lib.lpb_destroy.restype = None
     lib.lpb_last_error.restype = C.c_char_p
+    lib.lpb_scaling_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp]
     for f in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results", "lpb_result_device",
-              "lpb_batch_profile", "lpb_handle_info", "lpb_scaling"):
+              "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_scaling_noalloc"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -195,6 +196,15 @@ def lpb_scaling(h, m: int, n: int):
     dr, dc = np.zeros(max(m, 1)), np.zeros(n)
     _check(load().lpb_scaling(h, _ptr(dr), _ptr(dc)))
     return dr[:m], dc
+
+
+def lpb_scaling_noalloc(m: int, n: int, nnz: int, row_ptr_dev: int, col_idx_dev: int, vals_dev: int,
+                        ruiz_iters: int, pock_chambolle: int, d_row_dev: int, d_col_dev: int, stream=None) -> None:
+    """Equilibration factors into caller-owned device buffers, using the
+    library's fixed device scratch (no allocation).  Pointers are device
+    addresses (e.g. torch ``data_ptr()``); ``stream`` a cudaStream_t or None."""
+    _check(load().lpb_scaling_noalloc(int(m), int(n), int(nnz), row_ptr_dev, col_idx_dev, vals_dev,
+                                      int(ruiz_iters), int(pock_chambolle), d_row_dev, d_col_dev, stream))
 
 
 def lpb_batch_free(b) -> None:
