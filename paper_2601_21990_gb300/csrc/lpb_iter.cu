@@ -22,10 +22,9 @@
 // matrices X_lo, X_hi and C are never formed.
 //
 // The per-column parameters of the block's column tile are staged in shared
-// memory once per block.  No
-// FP64 instruction runs in the FP32 kernels (GB300 executes FP64 at a small
-// fraction of its FP32 rate); the Halpern weights come from a table written
-// by the check kernels.
+// memory once per block.  No FP64 instruction runs in the FP32 kernels
+// (GB300 executes FP64 at a small fraction of its FP32 rate); the Halpern
+// weights come from a table written by the check kernels.
 #include "lpb_internal.h"
 
 // resident blocks per SM the step kernels are compiled for (register cap)
