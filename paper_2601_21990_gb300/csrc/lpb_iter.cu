@@ -29,7 +29,7 @@
 
 // resident blocks per SM the step kernels are compiled for (register cap)
 #ifndef LPB_STEP_MIN_BLOCKS
-#define LPB_STEP_MIN_BLOCKS 1
+#define LPB_STEP_MIN_BLOCKS 5
 #endif
 
 namespace lpb {
@@ -63,59 +63,79 @@ __device__ __forceinline__ void stv(double* p, const double (&r)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
 }
 
-// acc += sum over the entries [beg, end) of a_e * src[col_e, col0 .. col0+V).
-// The G lanes of the row group load up to R = G*K of the row's (col, value)
-// pairs at once (K per lane, coalesced), then broadcast them by shuffle and
-// issue the gathers four at a time, so a row of up to R entries costs one
-// index round trip and a pipelined burst of gathers.
-template <typename T, int V, int G>
-__device__ __forceinline__ void gather_coop(const int* __restrict__ ci, const T* __restrict__ va,
-                                            const T* __restrict__ src, int ld, int col0, int beg, int end,
-                                            T (&acc)[V]) {
-    constexpr int K = G >= 16 ? 1 : 16 / G;
-    constexpr int R = G * K;
+// One round of a row's entries: the G lanes of the row group load up to
+// R = G*K of the row's (col, value) pairs at once (K per lane, coalesced);
+// narrow groups take rounds of 8 to bound the registers holding the entries.
+template <typename T, int G>
+struct Round {
+    static constexpr int K = G >= 8 ? 1 : 8 / G;
+    static constexpr int R = G * K;
+};
+
+template <typename T, int G>
+__device__ __forceinline__ void load_round(const int* __restrict__ ci, const T* __restrict__ va, int e0, int end,
+                                           int (&c)[Round<T, G>::K], T (&a)[Round<T, G>::K]) {
+    constexpr int K = Round<T, G>::K;
     const int lane = threadIdx.x % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int me = e0 + q * G + lane;
+        c[q] = me < end ? __ldg(ci + me) : 0;
+        a[q] = me < end ? __ldg(va + me) : T(0);
+    }
+}
+
+// acc += sum over the round's cnt entries of a_e * src[col_e, colg .. colg+V):
+// entries are broadcast by shuffle inside the row group (entry k sits in
+// register slot k / G of lane k % G, compile-time after unrolling) and the
+// gathers issued four at a time.  Entries past cnt get a = 0 and the round's
+// first column, so every gather stays in bounds.  All lanes of the group
+// must call it (lanes past the last LP pass the tile's first column).
+template <typename T, int V, int G>
+__device__ __forceinline__ void gather_round(const int (&c)[Round<T, G>::K], const T (&a)[Round<T, G>::K], int cnt,
+                                             const T* __restrict__ src, int ld, int colg, unsigned gmask,
+                                             T (&acc)[V]) {
+    constexpr int R = Round<T, G>::R;
+    const int cfirst = __shfl_sync(gmask, c[0], 0, G);
+#pragma unroll
+    for (int k0 = 0; k0 < R; k0 += 4) {
+        if (k0 >= cnt) break;
+        int cc[4];
+        T aa[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + j;
+            const int cs = __shfl_sync(gmask, c[k / G], k % G, G);
+            const T as = __shfl_sync(gmask, a[k / G], k % G, G);
+            cc[j] = k < cnt ? cs : cfirst;
+            aa[j] = k < cnt ? as : T(0);
+        }
+        T x0[V], x1[V], x2[V], x3[V];
+        ldg_v(src + (size_t)cc[0] * ld + colg, x0);
+        ldg_v(src + (size_t)cc[1] * ld + colg, x1);
+        ldg_v(src + (size_t)cc[2] * ld + colg, x2);
+        ldg_v(src + (size_t)cc[3] * ld + colg, x3);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            acc[v] = fma(aa[0], x0[v], acc[v]);
+            acc[v] = fma(aa[1], x1[v], acc[v]);
+            acc[v] = fma(aa[2], x2[v], acc[v]);
+            acc[v] = fma(aa[3], x3[v], acc[v]);
+        }
+    }
+}
+
+template <typename T, int V, int G>
+__device__ __forceinline__ void gather_range(const int* __restrict__ ci, const T* __restrict__ va,
+                                             const T* __restrict__ src, int ld, int colg, int beg, int end,
+                                             unsigned gmask, T (&acc)[V]) {
+    constexpr int K = Round<T, G>::K, R = Round<T, G>::R;
+#pragma unroll 1
     for (int e0 = beg; e0 < end; e0 += R) {
         int c[K];
         T a[K];
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const int me = e0 + q * G + lane;
-            c[q] = me < end ? __ldg(ci + me) : 0;
-            a[q] = me < end ? __ldg(va + me) : T(0);
-        }
-        const int cnt = min(R, end - e0);
-        // entry k of the round sits in register slot k / G of lane k % G
-        // (compile-time after unrolling); entries past cnt get a = 0 and the
-        // round's first column, so every gather stays in bounds
-        const int cfirst = __shfl_sync(gmask, c[0], 0, G);
-#pragma unroll
-        for (int k0 = 0; k0 < R; k0 += 4) {
-            if (k0 >= cnt) break;
-            int cc[4];
-            T aa[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = k0 + j;
-                const int cs = __shfl_sync(gmask, c[k / G], k % G, G);
-                const T as = __shfl_sync(gmask, a[k / G], k % G, G);
-                cc[j] = k < cnt ? cs : cfirst;
-                aa[j] = k < cnt ? as : T(0);
-            }
-            T x0[V], x1[V], x2[V], x3[V];
-            ldg_v(src + (size_t)cc[0] * ld + col0, x0);
-            ldg_v(src + (size_t)cc[1] * ld + col0, x1);
-            ldg_v(src + (size_t)cc[2] * ld + col0, x2);
-            ldg_v(src + (size_t)cc[3] * ld + col0, x3);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                acc[v] = fma(aa[0], x0[v], acc[v]);
-                acc[v] = fma(aa[1], x1[v], acc[v]);
-                acc[v] = fma(aa[2], x2[v], acc[v]);
-                acc[v] = fma(aa[3], x3[v], acc[v]);
-            }
-        }
+        load_round<T, G>(ci, va, e0, end, c, a);
+        gather_round<T, V, G>(c, a, min(R, end - e0), src, ld, colg, gmask, acc);
     }
 }
 
@@ -145,27 +165,6 @@ struct StepArgs {
     int t;
 };
 
-// Row handled by this thread's row group: a long row (whole block, row
-// groups split the nonzeros) or a short one.  Returns false when the group
-// has no row.
-template <int G>
-__device__ __forceinline__ bool pick_row(const int* __restrict__ rp, const int* __restrict__ long_rows, int n_long,
-                                         int rows, int& row, int& slot, int& nslot, bool& is_long) {
-    constexpr int GPB = kBlock / G;
-    const int grp = threadIdx.x / G;
-    is_long = (int)blockIdx.x < n_long;
-    if (is_long) {
-        row = long_rows[blockIdx.x];
-        slot = grp;
-        nslot = GPB;
-        return true;
-    }
-    row = ((int)blockIdx.x - n_long) * GPB + grp;
-    slot = 0;
-    nslot = 1;
-    return row < rows && rp[row + 1] - rp[row] <= kLongRow;
-}
-
 // Reduce the row groups' partial sums of a long row through shared memory;
 // on return only row group 0 holds the sum.  Every thread of the block calls it.
 template <typename T, int V, int G>
@@ -182,73 +181,42 @@ __device__ __forceinline__ bool long_row_reduce(T (&acc)[V], T* red) {
     return true;
 }
 
-template <typename T, int G, bool CHECK>
-__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_primal(const StepArgs<T> a) {
-    constexpr int V = Vec<T>::V, TN = G * V;
-    __shared__ T red[kBlock * V];
-    __shared__ T s_tau[TN], s_lo[TN], s_hi[TN], s_c[TN];
-    __shared__ int s_kind[TN], s_var[TN];
-    const int lane = threadIdx.x % G;
-    const int tile0 = blockIdx.y * TN;
-    for (int q = threadIdx.x; q < TN; q += kBlock) {
-        const int j = tile0 + q;
-        const bool in = j < a.ld;
-        s_kind[q] = in ? a.col.kind[j] : 0;
-        s_var[q] = in ? a.col.var[j] : -1;
-        s_tau[q] = in ? a.col.tau[j] : T(0);
-        s_lo[q] = in ? a.col.lo[j] : T(0);
-        s_hi[q] = in ? a.col.hi[j] : T(0);
-        s_c[q] = in ? a.col.c[j] : T(0);
-    }
-    __syncthreads();
-    const int col0 = tile0 + lane * V;
-    const bool active = col0 < a.ncol;
-    int row, slot, nslot;
-    bool is_long;
-    if (!pick_row<G>(a.rp, a.long_rows, a.n_long, a.rows, row, slot, nslot, is_long)) return;
-    const bool owner = active && (!is_long || slot == 0);
+template <typename T>
+__device__ __forceinline__ T barrier(T v, T lo, T hi) {
+    const bool li = isinf(lo), hi_ = isinf(hi);
+    if (li && hi_) return T(0);
+    if (li) return v > T(0) ? v : T(0);
+    if (hi_) return v < T(0) ? v : T(0);
+    return v;
+}
 
-    // the epilogue's operands, issued before the gather
+// per-column parameters of the block's column tile, staged in shared memory
+template <typename T, int TN>
+struct TileParams {
+    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN];
+    int kind[TN], var[TN];
+};
+
+// primal epilogue for row `row`, lane columns col0 .. col0+V (q0 = their
+// offset in the tile): box projection, reflection, Halpern update
+template <typename T, int V, int TN, bool CHECK>
+__device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const TileParams<T, TN>& P, int row, int col0,
+                                                int q0, const T (&acc)[V]) {
     const size_t off = (size_t)row * a.ld + col0;
-    T x[V], x0[V], cr = T(0), lor = T(0), hir = T(0);
-    auto load_epilogue = [&]() {
-        ldv(a.Z + off, x);
-        ldv(a.Z0 + off, x0);
-        cr = a.rc[row];
-        lor = a.rlo[row];
-        hir = a.rhi[row];
-    };
-    T acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = T(0);
-    {
-        // a long row is cut into nslot contiguous pieces, one per row group;
-        // every lane of a group takes part in its shuffles, so lanes past the
-        // last column gather the tile's first (valid) column and drop the sum
-        int beg = a.rp[row], end = a.rp[row + 1];
-        if (nslot > 1) {
-            const int piece = (end - beg + nslot - 1) / nslot;
-            beg = min(end, beg + slot * piece);
-            end = min(end, beg + piece);
-        }
-        gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
-    }
-    // the row's own operands are loaded after the gather: issuing them first
-    // keeps them live across it and costs occupancy (measured slower)
-    if (owner) load_epilogue();
-    if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
-    if (!active) return;
-
+    T x[V], x0[V];
+    ldv(a.Z + off, x);
+    ldv(a.Z0 + off, x0);
+    const T cr = a.rc[row], lor = a.rlo[row], hir = a.rhi[row];
     const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
     T xh[V], xb[V], xn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const int q = lane * V + v;
-        const int kind = s_kind[q], var = s_var[q];
+        const int q = q0 + v;
+        const int kind = P.kind[q], var = P.var[q];
         T cj = cr, lo = lor, hi = hir;
-        if (kind == 2) cj = var == row ? s_c[q] : T(0);
-        else if (kind == 1 && var == row) { lo = s_lo[q]; hi = s_hi[q]; }
-        const T step = s_tau[q] * (cj + acc[v]);
+        if (kind == 2) cj = var == row ? P.c[q] : T(0);
+        else if (kind == 1 && var == row) { lo = P.lo[q]; hi = P.hi[q]; }
+        const T step = P.tau[q] * (cj + acc[v]);
         T s = x[v] - step;
         const bool inside = s < hi && s > lo;
         s = s < hi ? s : hi;
@@ -269,68 +237,20 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_primal(const St
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T barrier(T v, T lo, T hi) {
-    const bool li = isinf(lo), hi_ = isinf(hi);
-    if (li && hi_) return T(0);
-    if (li) return v > T(0) ? v : T(0);
-    if (hi_) return v < T(0) ? v : T(0);
-    return v;
-}
-
-template <typename T, int G, bool CHECK>
-__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_dual(const StepArgs<T> a) {
-    constexpr int V = Vec<T>::V, TN = G * V;
-    __shared__ T red[kBlock * V];
-    __shared__ T s_sigma[TN];
-    const int lane = threadIdx.x % G;
-    const int tile0 = blockIdx.y * TN;
-    for (int q = threadIdx.x; q < TN; q += kBlock) {
-        const int j = tile0 + q;
-        s_sigma[q] = j < a.ld ? a.col.sigma[j] : T(1);
-    }
-    __syncthreads();
-    const int col0 = tile0 + lane * V;
-    const bool active = col0 < a.ncol;
-    int row, slot, nslot;
-    bool is_long;
-    if (!pick_row<G>(a.rp, a.long_rows, a.n_long, a.rows, row, slot, nslot, is_long)) return;
-    const bool owner = active && (!is_long || slot == 0);
-
+// dual epilogue: row projection and Halpern update
+template <typename T, int V, int TN, bool CHECK>
+__device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TileParams<T, TN>& P, int row, int col0,
+                                              int q0, const T (&acc)[V]) {
     const size_t off = (size_t)row * a.ld + col0;
-    T y[V], y0[V], lr = T(0), ur = T(0);
-    auto load_epilogue = [&]() {
-        ldv(a.Z + off, y);
-        ldv(a.Z0 + off, y0);
-        lr = a.rlo[row];
-        ur = a.rhi[row];
-    };
-    T acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = T(0);
-    {
-        // a long row is cut into nslot contiguous pieces, one per row group;
-        // every lane of a group takes part in its shuffles, so lanes past the
-        // last column gather the tile's first (valid) column and drop the sum
-        int beg = a.rp[row], end = a.rp[row + 1];
-        if (nslot > 1) {
-            const int piece = (end - beg + nslot - 1) / nslot;
-            beg = min(end, beg + slot * piece);
-            end = min(end, beg + piece);
-        }
-        gather_coop<T, V, G>(a.ci, a.va, a.src, a.ld, active ? col0 : tile0, beg, end, acc);
-    }
-    // the row's own operands are loaded after the gather: issuing them first
-    // keeps them live across it and costs occupancy (measured slower)
-    if (owner) load_epilogue();
-    if (is_long && !long_row_reduce<T, V, G>(acc, red)) return;
-    if (!active) return;
-
+    T y[V], y0[V];
+    ldv(a.Z + off, y);
+    ldv(a.Z0 + off, y0);
+    const T lr = a.rlo[row], ur = a.rhi[row];
     const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
     T yh[V], yn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const T sg = s_sigma[lane * V + v];
+        const T sg = P.sigma[q0 + v];
         const T s = y[v] / sg + acc[v];
         T p = s < ur ? s : ur;
         p = p > lr ? p : lr;
@@ -351,19 +271,120 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_dual(const Step
     }
 }
 
+// One step (primal or dual) of the iteration on one column tile.
+//   Blocks [0, n_long): one long row each, split into contiguous pieces over
+//   the block's row groups and reduced in shared memory.
+//   Blocks [n_long, gridDim.x): persistent over the short rows, row group g
+//   taking rows g, g + stride, ...; while it gathers and finishes a row, the
+//   row pointers and the first index round of its next row are in flight.
+template <typename T, int G, bool CHECK, bool PRIMAL>
+__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const StepArgs<T> a) {
+    constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
+    constexpr int K = Round<T, G>::K, R = Round<T, G>::R;
+    __shared__ T red[kBlock * V];
+    __shared__ TileParams<T, TN> P;
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int tile0 = blockIdx.y * TN;
+    for (int q = threadIdx.x; q < TN; q += kBlock) {
+        const int j = tile0 + q;
+        const bool in = j < a.ld;
+        if (PRIMAL) {
+            P.kind[q] = in ? a.col.kind[j] : 0;
+            P.var[q] = in ? a.col.var[j] : -1;
+            P.tau[q] = in ? a.col.tau[j] : T(0);
+            P.lo[q] = in ? a.col.lo[j] : T(0);
+            P.hi[q] = in ? a.col.hi[j] : T(0);
+            P.c[q] = in ? a.col.c[j] : T(0);
+        } else {
+            P.sigma[q] = in ? a.col.sigma[j] : T(1);
+        }
+    }
+    __syncthreads();
+    const int col0 = tile0 + lane * V;
+    const bool active = col0 < a.ncol;
+    const int colg = active ? col0 : tile0;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+
+    if ((int)blockIdx.x < a.n_long) {
+        const int row = a.long_rows[blockIdx.x];
+        const int rb = a.rp[row], re = a.rp[row + 1];
+        const int piece = (re - rb + GPB - 1) / GPB;
+        const int beg = min(re, rb + grp * piece), end = min(re, beg + piece);
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+        gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg, end, gmask, acc);
+        if (!long_row_reduce<T, V, G>(acc, red) || !active) return;
+        if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc);
+        else dual_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc);
+        return;
+    }
+
+    const int stride = ((int)gridDim.x - a.n_long) * GPB;
+    int r = ((int)blockIdx.x - a.n_long) * GPB + grp;
+    int beg = 0, end = 0;
+    int c[K];
+    T av[K];
+    if (r < a.rows) {
+        beg = a.rp[r];
+        end = a.rp[r + 1];
+        load_round<T, G>(a.ci, a.va, beg, end - beg <= kLongRow ? end : beg, c, av);
+    }
+#pragma unroll 1
+    while (r < a.rows) {
+        const int rn = r + stride;
+        int nbeg = 0, nend = 0;
+        if (rn < a.rows) {
+            nbeg = a.rp[rn];
+            nend = a.rp[rn + 1];
+        }
+        const bool is_short = end - beg <= kLongRow;
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+        if (is_short) {
+            gather_round<T, V, G>(c, av, min(R, end - beg), a.src, a.ld, colg, gmask, acc);
+            if (end - beg > R)
+                gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg + R, end, gmask, acc);
+        }
+        // the next row's first index round, issued before this row's epilogue
+        if (rn < a.rows) load_round<T, G>(a.ci, a.va, nbeg, nend - nbeg <= kLongRow ? nend : nbeg, c, av);
+        if (is_short && active) {
+            if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc);
+            else dual_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc);
+        }
+        r = rn;
+        beg = nbeg;
+        end = nend;
+    }
+}
+
+template <typename T, int G, bool CHECK, bool PRIMAL>
+cudaError_t launch_k(const StepArgs<T>& a, cudaStream_t s) {
+    constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
+    // resident blocks per SM and SM count, looked up once per instantiation
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0, b = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<T, G, CHECK, PRIMAL>, kBlock, 0) != cudaSuccess)
+            return cudaGetLastError();
+        sms = n > 0 ? n : 1;
+        per_sm = b > 0 ? b : 1;
+    }
+    const int need = (a.rows + GPB - 1) / GPB;
+    const int persist = need < sms * per_sm ? need : sms * per_sm;
+    dim3 grid(a.n_long + persist, (a.ncol + TN - 1) / TN);
+    k_step<T, G, CHECK, PRIMAL><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T, int G>
 cudaError_t launch_step(bool primal, bool check, const StepArgs<T>& a, cudaStream_t s) {
-    constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
     if (a.rows == 0 || a.ncol == 0) return cudaSuccess;
-    dim3 grid(a.n_long + (a.rows + GPB - 1) / GPB, (a.ncol + TN - 1) / TN);
-    if (primal) {
-        if (check) k_primal<T, G, true><<<grid, kBlock, 0, s>>>(a);
-        else k_primal<T, G, false><<<grid, kBlock, 0, s>>>(a);
-    } else {
-        if (check) k_dual<T, G, true><<<grid, kBlock, 0, s>>>(a);
-        else k_dual<T, G, false><<<grid, kBlock, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (primal) return check ? launch_k<T, G, true, true>(a, s) : launch_k<T, G, false, true>(a, s);
+    return check ? launch_k<T, G, true, false>(a, s) : launch_k<T, G, false, false>(a, s);
 }
 
 template <typename T>
