@@ -182,13 +182,159 @@ def cpu_baseline(w, cores, budget_lps):
             "sample": f"{sample} of {q} LPs of {w.name}, each alone, OpenMP over LPs, {dt:.1f} s"}
 
 
+def run_serving(args, rank, world, local):
+    """Continuous batching over five matrices (m = 1k .. 200k, n = 2m, power-
+    law rows): first the capacity with every request queued at once, then a
+    seeded Poisson stream at args.load of that capacity; latency is each
+    request's submit-to-done time.  Every request warm-starts from its
+    matrix's base LP, solved first and kept on the device."""
+    import torch
+
+    from paper_2601_21990_gb300 import lpb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    mats = lpgen.serving_matrices(seed0=args.seed + 10 * rank)
+    handles = [lpb.Handle(lp, precision=lpb.MIXED, device=local) for lp in mats]
+    srv = lpb.Server(lane_columns=512, polish_columns=64, max_groups=64, device=local)
+    mids = [srv.attach(h) for h in handles]
+    parents = [srv.submit(mid, lpb.specs_array([0], [-1]), tol=TOL, max_iter=100000) for mid in mids]
+    for p in parents:
+        srv.wait(p)
+    specs_np = {}
+
+    def submit(k, sp):
+        key = id(sp)
+        if key not in specs_np:
+            specs_np[key] = lpb.specs_from(sp)
+        return srv.submit(mids[k], specs_np[key], tol=TOL, max_iter=100000, warm_request=parents[k], warm_lp=0)
+
+    def drain(ids):
+        solved, d2h = 0, 0
+        for r in ids:
+            srv.wait(r)
+            res = srv.results(r)
+            d2h += res.nbytes
+            solved += solved_count(res)
+        return solved, d2h
+
+    warm = lpgen.serving_stream(mats, seed=99, count=max(args.warmup, 1) * 5)
+    for r in [submit(k, sp) for _, k, sp in warm]:
+        srv.wait(r)
+        srv.release(r)
+    # capacity: everything queued at once; the rate while 80% of the LPs
+    # finish (the last few requests alone would measure their latency)
+    cap_stream = lpgen.serving_stream(mats, seed=101, count=max(args.requests // 2, 10))
+    cap_ids = [submit(k, sp) for _, k, sp in cap_stream]
+    done = []
+    for r in cap_ids:
+        srv.wait(r)
+        info = srv.info(r)
+        done.append((info.t_done, info.t_submit, solved_count(srv.results(r))))
+        srv.release(r)
+    t_first = min(d[1] for d in done)
+    done.sort()
+    tot = sum(d[2] for d in done)
+    acc, cap = 0, None
+    for t_d, _, c in done:
+        acc += c
+        if acc >= 0.8 * tot:
+            cap = acc / max(t_d - t_first, 1e-9)
+            break
+    stream = lpgen.serving_stream(mats, seed=100, count=args.requests)
+    mean_lps = float(np.mean([len(sp) for _, _, sp in stream]))
+    rate = args.load * cap / mean_lps  # requests per second
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    st0 = srv.stats()
+    ids, t_sub = [], []
+    t0 = time.perf_counter()
+    t_next = t0
+    h2d = 0
+    for gap, k, sp in stream:
+        t_next += gap / rate
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(submit(k, sp))
+        h2d += specs_np[id(sp)].nbytes
+    nsolved, d2h = drain(ids)
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st1 = srv.stats()
+    lat, per_mat = [], {}
+    for (gap, k, sp), r in zip(stream, ids):
+        info = srv.info(r)
+        lat.append(1e3 * (info.t_done - info.t_submit))
+        per_mat.setdefault(k, []).append((lat[-1], 1e3 * (info.t_admit - info.t_submit), info.iters,
+                                          info.polished))
+        srv.release(r)
+    total_s = wall
+    if dist:
+        t = torch.tensor([wall], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        c = torch.tensor([nsolved], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(c)
+        nsolved_all = int(c.item())
+    else:
+        nsolved_all = nsolved
+    value = nsolved_all / total_s
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-iterates/f64-checks", "data": "synthetic",
+            "config": {"workload": "serving: 5 power-law matrices m=1k..200k n=2m, Poisson requests of U{1..256} "
+                                   "strong-branching children, warm start from the parent LP on the device",
+                       "requests": len(ids), "lps": int(sum(len(sp) for _, _, sp in stream)), "tol": TOL,
+                       "load": args.load, "capacity_lps_per_s": cap, "rate_req_per_s": rate,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs (200k-row matrix lanes) exceed L2"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(np.max(lat)), "what": "request submit to done"},
+            "latency_by_matrix": {f"m={mats[k].m}": {
+                "requests": len(v), "p50_ms": float(np.percentile([a[0] for a in v], 50)),
+                "p99_ms": float(np.percentile([a[0] for a in v], 99)),
+                "queue_p50_ms": float(np.percentile([a[1] for a in v], 50)),
+                "iters_p50": float(np.percentile([a[2] for a in v], 50)),
+                "polished": int(sum(a[3] for a in v))} for k, v in sorted(per_mat.items())},
+            "server": {"intervals": st1.intervals - st0.intervals,
+                       "admitted_while_busy": st1.admitted_while_busy - st0.admitted_while_busy,
+                       "migrations": st1.migrations - st0.migrations,
+                       "column_iters": st1.column_iters - st0.column_iters,
+                       "busy_frac": (st1.busy_s - st0.busy_s) / wall},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "what": "the serving API itself: host records in, host results out"},
+            "gpu_launches": int(st1.kernels - st0.kernels),
+            "clocks": clk,
+        }), flush=True)
+    srv.close()
+
+
+def solved_count(res) -> int:
+    st = res["status"]
+    return int(np.sum((st == 0) | (st == 1) | (st == 2)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sb_powerlaw", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sb_powerlaw", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=160, help="serving: requests in the timed Poisson stream")
+    ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate as a fraction of capacity")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-lps", type=int, default=64)
     ap.add_argument("--ref-warmup", action="store_true")
@@ -198,7 +344,14 @@ def main():
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
+        if args.workload == "serving":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop; the reference "
+                              "arm runs on the batch workloads"}), flush=True)
+            return
         run_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
 
     import torch
@@ -342,6 +495,8 @@ def main():
                     "what": "lpb_create from host CSR + lpb_solve from host records + lpb_results"},
             "gpu_launches": gpu_launches,
             "setup_ms": setup_ms,
+            "polish": {"arith": "dfloat" if opts.polish_arith == lpb.POLISH_DFLOAT else "fp64",
+                       "switch_iter_per_step": [int(p.fp64_switch_iter) for p in profs]},
             "clocks": clk,
         }
     if dist:

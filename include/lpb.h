@@ -75,11 +75,17 @@ typedef struct {
     int32_t profile;                /* 1: time every iteration kernel with CUDA events */
     void* cuda_stream;              /* cudaStream_t to run on, or NULL */
     int32_t device;                 /* CUDA device ordinal, or -1 for the current device */
-    int32_t fp64_polish;            /* LPB_MIXED only: 1 (default) widens the remaining batch to FP64
-                                       iterates once an LP stalls at FP32 resolution */
+    int32_t fp64_polish;            /* LPB_MIXED only: 1 (default) widens the remaining batch to
+                                       FP64-accurate iterates once an LP stalls at FP32 resolution */
     int32_t polish_stall_checks;    /* an LP stalls when its KKT error has not halved over this many
                                        checks (default 32) */
+    int32_t polish_arith;           /* arithmetic of the polish iterates: LPB_POLISH_DFLOAT (default;
+                                       double-float pairs on the FP32 pipe, 8 bytes per value) or
+                                       LPB_POLISH_FP64 (native FP64) */
 } lpb_options;
+
+/* Values of lpb_options.polish_arith. */
+enum { LPB_POLISH_DFLOAT = 0, LPB_POLISH_FP64 = 1 };
 
 /* One override record (Sec. 5.1, 5.2). */
 typedef struct {

@@ -376,6 +376,34 @@ def from_dense(a: np.ndarray, c, row_lo, row_hi, var_lo, var_hi, name: str = "")
     return LPData(m, n, row_ptr, ci, vv, f(c), f(row_lo), f(row_hi), f(var_lo), f(var_hi), None, name)
 
 
+# rows of the five serving matrices: geometric from 1k to 200k
+SERVING_ROWS = (1000, 3760, 14100, 53200, 200000)
+
+
+def serving_matrices(seed0: int = 0, rows=SERVING_ROWS):
+    """The serving set: matrices built like ``sb_powerlaw`` with m rows and
+    n = 2m columns (power-law row lengths on [2, 500], mean 12.5), seeds
+    seed0 .. seed0+4."""
+    return [sb_powerlaw_matrix(seed0 + k, m, 2 * m, f"serve{k}_m{m}") for k, m in enumerate(rows)]
+
+
+def serving_stream(mats, seed: int = 100, count: int = 200, max_children: int = 256):
+    """A seeded request stream over ``mats``: unit-rate exponential
+    inter-arrival gaps (scale them by 1/rate), a uniformly drawn matrix and
+    U{1..max_children} strong-branching children (random columns x {up,
+    down}) per request.  Returns [(gap, matrix index, Specs)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        gap = float(rng.exponential(1.0))
+        k = int(rng.integers(len(mats)))
+        b = int(rng.integers(1, max_children + 1))
+        lp = mats[k]
+        cand = rng.choice(lp.n, size=(b + 1) // 2, replace=False)
+        out.append((gap, k, sb_specs(lp.x0, cand).subset(range(b))))
+    return out
+
+
 WORKLOADS = {
     "sb_small": sb_small,
     "sb_powerlaw": sb_powerlaw,

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "lpb")
 LIB = os.path.join(PKG, "liblpb.so")
-SOURCES = ["lpb_api.cu", "lpb_setup.cu", "lpb_iter.cu", "lpb_check.cu", "lpb_noalloc.cu"]
+SOURCES = ["lpb_api.cu", "lpb_engine.cu", "lpb_serve.cu", "lpb_setup.cu", "lpb_iter.cu", "lpb_check.cu", "lpb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,7 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    files.append(os.path.join(INCLUDE, "lpb.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return files
 

@@ -9,9 +9,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
-#include "lpb_internal.h"
+#include "lpb_engine.h"
 
 using namespace lpb;
 
@@ -19,21 +20,7 @@ namespace {
 
 thread_local std::string g_err;
 
-lpb_err fail(lpb_err code, const std::string& msg) {
-    g_err = msg;
-    return code;
-}
-
-lpb_err cuda_fail(cudaError_t e, const char* what) {
-    return fail(e == cudaErrorMemoryAllocation ? LPB_ERR_OOM : LPB_ERR_CUDA,
-                std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define CU(call)                                              \
-    do {                                                      \
-        cudaError_t _e = (call);                              \
-        if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
-    } while (0)
+#define CU(call) LPB_CU(call)
 
 struct DeviceGuard {
     int prev = -1;
@@ -46,63 +33,6 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
-
-size_t rup(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-}  // namespace
-
-struct lpb_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    lpb_options opt{};
-    int m = 0, n = 0, nnz = 0;
-    Csr A, At;
-    double *d_r = nullptr, *d_c = nullptr;
-    double *c = nullptr, *l = nullptr, *u = nullptr, *xl = nullptr, *xu = nullptr;
-    double *cs = nullptr, *ls = nullptr, *us = nullptr, *xls = nullptr, *xus = nullptr;
-    float *cs32 = nullptr, *ls32 = nullptr, *us32 = nullptr, *xls32 = nullptr, *xus32 = nullptr;
-    // double-float copies for the checks of FP32 iterates
-    df *f_dr = nullptr, *f_dc = nullptr, *f_idr = nullptr, *f_idc = nullptr, *f_c = nullptr;
-    df *f_xl = nullptr, *f_xu = nullptr, *f_l = nullptr, *f_u = nullptr;
-    double eta = 0.0, norm_est = 0.0, c_norm_base = 0.0, b_norm = 0.0, setup_ms = 0.0;
-    int power_iters = 0;
-    std::vector<void*> fixed_allocs;
-    // per-capacity workspace
-    int cap = 0, ld = 0;
-    std::vector<void*> ws_allocs;
-    // iterate buffers and per-column parameters in each precision: [0] FP32
-    // (mixed path), [1] FP64 (FP64 path, and the mixed path's FP64 polish)
-    struct Set {
-        void *X = nullptr, *X0 = nullptr, *Xbar = nullptr, *Xh = nullptr, *DX = nullptr;
-        void *Y = nullptr, *Y0 = nullptr, *Yh = nullptr, *DY = nullptr, *DYp = nullptr;
-        void *clo = nullptr, *chi = nullptr, *cc = nullptr, *ctau = nullptr, *csigma = nullptr;
-    } set[2];
-    double *P = nullptr, *Q = nullptr, *partials = nullptr, *colsum = nullptr;
-    int *ckind = nullptr, *cvar = nullptr, *clp = nullptr, *k_stall = nullptr;
-    double *k_lo = nullptr, *k_hi = nullptr, *k_c = nullptr, *k_w = nullptr, *k_best = nullptr;
-    double* hal64 = nullptr;   // Halpern weights of the next interval
-    float* hal32 = nullptr;
-    ColRecord* rec = nullptr;
-    Control* ctl = nullptr;
-    int* mv = nullptr;
-    lpb_lp_spec* specs_dev = nullptr;
-    ColRecord* rec_h = nullptr;
-    Control* ctl_h = nullptr;
-    int* mv_h = nullptr;
-    std::vector<cudaEvent_t> events;
-};
-
-struct lpb_batch {
-    int device = 0;
-    int num_lps = 0, m = 0, n = 0;
-    std::vector<lpb_lp_result> res;
-    double* x = nullptr;
-    double* y = nullptr;
-    lpb_profile prof{};
-};
-
-namespace {
 
 template <typename P>
 cudaError_t dmalloc(std::vector<void*>& list, P** out, size_t count) {
@@ -118,310 +48,66 @@ void free_list(std::vector<void*>& list) {
     list.clear();
 }
 
-void free_workspace(lpb_ctx* h) {
-    free_list(h->ws_allocs);
-    if (h->rec_h) cudaFreeHost(h->rec_h);
-    if (h->ctl_h) cudaFreeHost(h->ctl_h);
-    if (h->mv_h) cudaFreeHost(h->mv_h);
-    h->rec_h = nullptr;
-    h->ctl_h = nullptr;
-    h->mv_h = nullptr;
-    h->cap = h->ld = 0;
-}
+}  // namespace
 
-bool polish_enabled(const lpb_ctx* h) { return h->opt.precision == LPB_MIXED && h->opt.fp64_polish; }
-
-lpb_err ensure_workspace(lpb_ctx* h, int num_lps) {
-    if (num_lps <= h->cap) return LPB_OK;
-    free_workspace(h);
-    const int cap = (int)rup((size_t)num_lps, 4);
-    const int ld = cap;
-    const size_t mr = h->m > 0 ? (size_t)h->m : 1;
-    auto& L = h->ws_allocs;
-    for (int p = 0; p < 2; ++p) {
-        const bool need = p == 1 ? (h->opt.precision == LPB_FP64 || polish_enabled(h)) : h->opt.precision == LPB_MIXED;
-        if (!need) continue;
-        const size_t tsz = p == 0 ? sizeof(float) : sizeof(double);
-        auto& S = h->set[p];
-        void** xs[] = {&S.X, &S.X0, &S.Xbar, &S.Xh, &S.DX};
-        for (void** q : xs) CU(dmalloc(L, (char**)q, (size_t)h->n * ld * tsz));
-        void** ys[] = {&S.Y, &S.Y0, &S.Yh, &S.DY, &S.DYp};
-        for (void** q : ys) CU(dmalloc(L, (char**)q, mr * ld * tsz));
-        void** cs[] = {&S.clo, &S.chi, &S.cc, &S.ctau, &S.csigma};
-        for (void** q : cs) CU(dmalloc(L, (char**)q, tsz * ld));
-    }
-    CU(dmalloc(L, &h->P, sizeof(double) * 2 * mr * ld));
-    CU(dmalloc(L, &h->Q, sizeof(double) * 3 * (size_t)h->n * ld));
-    CU(dmalloc(L, &h->partials, sizeof(double) * (size_t)kNumStats * kReduceBlocks * ld));
-    CU(dmalloc(L, &h->colsum, sizeof(double) * (size_t)kNumStats * ld));
-    CU(dmalloc(L, &h->ckind, sizeof(int) * ld));
-    CU(dmalloc(L, &h->cvar, sizeof(int) * ld));
-    CU(dmalloc(L, &h->clp, sizeof(int) * ld));
-    CU(dmalloc(L, &h->k_stall, sizeof(int) * ld));
-    CU(dmalloc(L, &h->k_lo, sizeof(double) * ld));
-    CU(dmalloc(L, &h->k_hi, sizeof(double) * ld));
-    CU(dmalloc(L, &h->k_c, sizeof(double) * ld));
-    CU(dmalloc(L, &h->k_w, sizeof(double) * ld));
-    CU(dmalloc(L, &h->k_best, sizeof(double) * ld));
-    CU(dmalloc(L, &h->hal64, sizeof(double) * 2 * (size_t)h->opt.check_every));
-    CU(dmalloc(L, &h->hal32, sizeof(float) * 2 * (size_t)h->opt.check_every));
-    CU(dmalloc(L, &h->rec, sizeof(ColRecord) * ld));
-    CU(dmalloc(L, &h->ctl, sizeof(Control)));
-    CU(dmalloc(L, &h->mv, sizeof(int) * 4 * ld));
-    CU(dmalloc(L, &h->specs_dev, sizeof(lpb_lp_spec) * ld));
-    CU(cudaMallocHost((void**)&h->rec_h, sizeof(ColRecord) * ld));
-    CU(cudaMallocHost((void**)&h->ctl_h, sizeof(Control)));
-    CU(cudaMallocHost((void**)&h->mv_h, sizeof(int) * 4 * ld));
-    h->cap = cap;
-    h->ld = ld;
-    return LPB_OK;
-}
-
-template <typename T> const T* pick(const double* d64, const float* d32);
-template <> const double* pick<double>(const double* d64, const float*) { return d64; }
-template <> const float* pick<float>(const double*, const float* d32) { return d32; }
-template <typename T> constexpr int set_of() { return sizeof(T) == sizeof(float) ? 0 : 1; }
-
-template <typename T>
-IterData<T> iter_data(const lpb_ctx* h) {
-    const auto& S = h->set[set_of<T>()];
-    IterData<T> d{};
-    d.A = h->A;
-    d.At = h->At;
-    d.a_vals = pick<T>(h->A.v64, h->A.v32);
-    d.at_vals = pick<T>(h->At.v64, h->At.v32);
-    d.c = pick<T>(h->cs, h->cs32);
-    d.xl = pick<T>(h->xls, h->xls32);
-    d.xu = pick<T>(h->xus, h->xus32);
-    d.l = pick<T>(h->ls, h->ls32);
-    d.u = pick<T>(h->us, h->us32);
-    d.col.kind = h->ckind;
-    d.col.var = h->cvar;
-    d.col.lo = (T*)S.clo;
-    d.col.hi = (T*)S.chi;
-    d.col.c = (T*)S.cc;
-    d.col.tau = (T*)S.ctau;
-    d.col.sigma = (T*)S.csigma;
-    return d;
-}
-
-template <typename T>
-IterBufs<T> iter_bufs(const lpb_ctx* h) {
-    const auto& S = h->set[set_of<T>()];
-    IterBufs<T> b{};
-    b.X = (T*)S.X;
-    b.X0 = (T*)S.X0;
-    b.Xbar = (T*)S.Xbar;
-    b.Y = (T*)S.Y;
-    b.Y0 = (T*)S.Y0;
-    b.Xh = (T*)S.Xh;
-    b.DX = (T*)S.DX;
-    b.G = nullptr;
-    b.Yh = (T*)S.Yh;
-    b.DY = (T*)S.DY;
-    b.DYp = (T*)S.DYp;
-    return b;
-}
-
-CheckData check_data(const lpb_ctx* h, double tol) {
-    CheckData d{};
-    d.A = h->A;
-    d.At = h->At;
-    d.m = h->m;
-    d.n = h->n;
-    d.d_r = h->d_r;
-    d.d_c = h->d_c;
-    d.c = h->c;
-    d.xl = h->xl;
-    d.xu = h->xu;
-    d.l = h->l;
-    d.u = h->u;
-    d.col.kind = h->ckind;
-    d.col.var = h->cvar;
-    d.col.lo = h->k_lo;
-    d.col.hi = h->k_hi;
-    d.col.c = h->k_c;
-    d.col.w = h->k_w;
-    d.col.lp = h->clp;
-    d.col.best = h->k_best;
-    d.col.stall = h->k_stall;
-    d.eta = h->eta;
-    d.beta_s = h->opt.beta_s;
-    d.beta_n = h->opt.beta_n;
-    d.beta_a = h->opt.beta_a;
-    d.theta = h->opt.theta;
-    d.mnorm_sign = h->opt.mnorm_sign;
-    d.eps_inf = h->opt.eps_infeas >= 0.0 ? h->opt.eps_infeas : tol;
-    d.tol = tol;
-    d.detect_inf = h->opt.detect_infeasibility;
-    d.restart_to_output = h->opt.restart_to_pdhg_output;
-    d.stall_checks = 0;
-    d.check_every = h->opt.check_every;
-    d.hal64 = h->hal64;
-    d.hal32 = h->hal32;
-    d.f_dr = h->f_dr;
-    d.f_dc = h->f_dc;
-    d.f_idr = h->f_idr;
-    d.f_idc = h->f_idc;
-    d.f_c = h->f_c;
-    d.f_xl = h->f_xl;
-    d.f_xu = h->f_xu;
-    d.f_l = h->f_l;
-    d.f_u = h->f_u;
-    return d;
-}
-
-double step_bytes(bool fp32, int nnz, int m, int n, bool primal, bool check, int ncol) {
-    const double ts = fp32 ? 4.0 : 8.0;
-    const double rows = primal ? n : m, cols = primal ? m : n;
-    double b = (4.0 + ts) * nnz + 4.0 * (rows + 1);
-    // gathered block once, plus the row-side operands: primal reads X, X0 and
-    // writes X, Xbar; dual reads Y, Y0 and writes Y; a check writes x^, dx
-    // (primal) or y^, dy, Pi_B(dy) (dual)
-    b += ts * ncol * (cols + rows * (primal ? 4.0 : 3.0) + (check ? (primal ? 2.0 : 3.0) * rows : 0.0));
-    return b;
-}
-
-void set_result(lpb_lp_result& r, const ColRecord& rc, int status, int64_t iters, int64_t restarts) {
-    r.status = status;
-    r.restarts = (int32_t)restarts;
-    r.iters = iters;
-    r.obj = rc.obj;
-    r.dual_obj = rc.dual_obj;
-    r.rel_primal = rc.rel_primal;
-    r.rel_dual = rc.rel_dual;
-    r.rel_gap = rc.rel_gap;
-}
-
-// State of one solve that survives a change of iterate precision.
-struct SolveState {
-    std::vector<int> colmap;  // column -> LP index
-    int ncol = 0;
-    int64_t K = 0;            // iterations done
-    bool done = false;
+struct lpb_batch {
+    int device = 0;
+    int num_lps = 0, m = 0, n = 0;
+    std::vector<lpb_lp_result> res;
+    double* x = nullptr;
+    double* y = nullptr;
+    lpb_profile prof{};
 };
 
-template <typename T>
-lpb_err compact(lpb_ctx* h, SolveState& st, const std::vector<int>& fin, lpb_profile& prof) {
-    if (fin.empty()) return LPB_OK;
-    const int ncol = st.ncol;
-    std::vector<char> is_fin(ncol, 0);
-    for (int f : fin) is_fin[f] = 1;
-    const int ncol2 = ncol - (int)fin.size();
-    int* src = h->mv_h;
-    int* dst = h->mv_h + h->ld;
-    int cnt = 0, tail = ncol - 1;
-    for (int f : fin) {
-        if (f >= ncol2) break;
-        while (is_fin[tail]) --tail;
-        src[cnt] = tail;
-        dst[cnt] = f;
-        st.colmap[f] = st.colmap[tail];
-        ++cnt;
-        --tail;
-    }
-    st.ncol = ncol2;
-    if (cnt == 0) return LPB_OK;
-    CU(cudaMemcpyAsync(h->mv, src, sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->mv + h->ld, dst, sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
-    IterData<T> id = iter_data<T>(h);
-    CheckData cd = check_data(h, 1.0);
-    CU(launch_compact<T>(iter_bufs<T>(h), h->n, h->m, h->ld, h->mv, h->mv + h->ld, cnt, id.col, cd.col, h->stream));
-    prof.compactions += 1;
-    prof.kernels += 2;
-    return LPB_OK;
+namespace {
+
+template <typename T> constexpr int prec_of() {
+    return std::is_same<T, float>::value ? kPrecF32 : std::is_same<T, double>::value ? kPrecF64 : kPrecDfl;
 }
 
-// Runs checked intervals in precision T until the batch is done, max_iter is
-// reached, or (FP32 with polish enabled) an LP stalls.  Returns with
-// st.done = false only in the last case.
-template <typename T>
-lpb_err run_phase(lpb_ctx* h, SolveState& st, double tol, int64_t max_iter, lpb_batch* bt) {
-    lpb_err rc;
-    cudaStream_t s = h->stream;
-    const int m = h->m, ld = h->ld;
-    IterData<T> id = iter_data<T>(h);
-    IterBufs<T> ib = iter_bufs<T>(h);
-    CheckData cd = check_data(h, tol);
-    const bool can_promote = sizeof(T) == sizeof(float) && polish_enabled(h);
-    if (can_promote) cd.stall_checks = h->opt.polish_stall_checks;
-    lpb_profile& prof = bt->prof;
-    const bool profile = h->opt.profile != 0;
+lpb_err ensure_events(lpb_ctx* h) {
     const int ce = h->opt.check_every;
-    const bool fp32 = sizeof(T) == sizeof(float);
-    std::vector<int> fin;
-    while (st.ncol > 0 && st.K < max_iter) {
-        const int L = (int)std::min<int64_t>(ce, max_iter - st.K);
-        for (int t = 0; t < L; ++t) {
-            const bool chk = t == L - 1;
-            CU(launch_iteration<T>(id, ib, ld, st.ncol, pick<T>(h->hal64, h->hal32), t, chk, s,
-                                   profile ? &h->events[3 * t] : nullptr));
-            prof.launches[0] += 1;
-            prof.launches[1] += m > 0 ? 1 : 0;
-            prof.kernels += m > 0 ? 2 : 1;
-            prof.bytes[0] += step_bytes(fp32, h->nnz, m, h->n, true, chk, st.ncol);
-            prof.bytes[1] += step_bytes(fp32, h->nnz, m, h->n, false, chk, st.ncol);
-        }
-        CU(launch_check<T>(cd, ib, ld, st.ncol, st.K + L - 1, L, st.K + L == max_iter, h->P, h->Q, h->partials,
-                           h->colsum, h->rec, h->ctl, id.col, s, profile ? &h->events[3 * L] : nullptr));
-        prof.launches[2] += m > 0 ? 2 : 1;
-        prof.launches[3] += 1;
-        prof.checks += 1;
-        prof.kernels += (m > 0 ? 2 : 1) + (m > 0 ? 1 : 0) + 1 + 1 + 1 + (m > 0 ? 2 : 1);
-        CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * st.ncol, cudaMemcpyDeviceToHost, s));
-        CU(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        if (profile) {
-            float ms = 0.f;
-            for (int t = 0; t < L; ++t) {
-                CU(cudaEventElapsedTime(&ms, h->events[3 * t], h->events[3 * t + 1]));
-                prof.ms[0] += ms;
-                CU(cudaEventElapsedTime(&ms, h->events[3 * t + 1], h->events[3 * t + 2]));
-                prof.ms[1] += ms;
-            }
-            CU(cudaEventElapsedTime(&ms, h->events[3 * L], h->events[3 * L + 1]));
-            prof.ms[2] += ms;
-            CU(cudaEventElapsedTime(&ms, h->events[3 * L + 1], h->events[3 * L + 2]));
-            prof.ms[3] += ms;
-        }
-        st.K += L;
-        const int64_t restarts_before = h->ctl_h->restarts - h->ctl_h->restart;
-        fin.clear();
-        for (int j = 0; j < st.ncol; ++j) {
-            int sj = h->rec_h[j].status;
-            if (sj < 0 && st.K >= max_iter) sj = LPB_ITERATION_LIMIT;
-            if (sj >= 0) {
-                set_result(bt->res[st.colmap[j]], h->rec_h[j], sj, st.K, restarts_before);
-                fin.push_back(j);
-            }
-        }
-        if (!fin.empty()) {
-            int* cols = h->mv_h + 2 * ld;
-            int* lps = h->mv_h + 3 * ld;
-            for (size_t q = 0; q < fin.size(); ++q) {
-                cols[q] = fin[q];
-                lps[q] = st.colmap[fin[q]];
-            }
-            const int cnt = (int)fin.size();
-            CU(cudaMemcpyAsync(h->mv + 2 * ld, cols, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-            CU(cudaMemcpyAsync(h->mv + 3 * ld, lps, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-            CU(launch_extract<T>(cd, ib, ld, h->mv + 2 * ld, h->mv + 3 * ld, cnt, h->xl, h->xu, bt->x, bt->y, s));
-            prof.kernels += 1;
-            if ((rc = compact<T>(h, st, fin, prof)) != LPB_OK) return rc;
-        }
-        if (can_promote && h->ctl_h->stalled && st.ncol > 0 && st.K < max_iter) return LPB_OK;
-    }
-    st.done = true;
+    if (!h->opt.profile || (int)h->events.size() >= 3 * ce + 3) return LPB_OK;
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    h->events.assign(3 * ce + 3, nullptr);
+    for (auto& e : h->events) CU(cudaEventCreate(&e));
     return LPB_OK;
 }
 
+// Runs checked intervals of lane ln until group g is done or (with can_stall)
+// it stalls; returns done = false only in the second case.
+template <typename T>
+lpb_err run_group(lpb_ctx* h, Lane& ln, GroupRun& g, std::vector<GroupRun*>& groups, bool can_stall, bool& done,
+                  lpb_profile& prof) {
+    cudaStream_t s = h->stream;
+    const int ce = h->opt.check_every;
+    const int stall_checks = can_stall ? h->opt.polish_stall_checks : 0;
+    lpb_err rc;
+    done = false;
+    while (g.live > 0) {
+        const int L = (int)std::min<int64_t>(ce, g.max_iter - g.K);
+        if ((rc = lane_interval<T>(h, ln, L, stall_checks, s, &prof)) != LPB_OK) return rc;
+        CU(cudaStreamSynchronize(s));
+        add_interval_times(h, L, &prof);
+        if ((rc = lane_collect<T>(h, ln, groups, s, &prof)) != LPB_OK) return rc;
+        if (can_stall && g.live > 0 && g.stalled) return LPB_OK;
+    }
+    done = true;
+    return LPB_OK;
+}
+
+// A batched solve: the batch is one restart group on the handle's lane of
+// its precision; with polish, a stalled batch moves to the polish lane.
 template <typename T>
 lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double tol, int64_t max_iter,
                    const double* wx, const double* wy, lpb_batch* bt) {
     lpb_err rc;
-    if ((rc = ensure_workspace(h, num_lps)) != LPB_OK) return rc;
     cudaStream_t s = h->stream;
-    const int n = h->n, m = h->m, ld = h->ld;
+    const int n = h->n, m = h->m;
+    Lane& ln = h->lane[prec_of<T>()];
+    if ((rc = lane_reserve(h, ln, prec_of<T>(), num_lps, 1)) != LPB_OK) return rc;
+    if ((rc = ensure_check_ws(h, ln.cap)) != LPB_OK) return rc;
+    if ((rc = ensure_events(h)) != LPB_OK) return rc;
     CU(cudaMalloc((void**)&bt->x, sizeof(double) * (size_t)n * (num_lps ? num_lps : 1)));
     CU(cudaMalloc((void**)&bt->y, sizeof(double) * (size_t)(m ? m : 1) * (num_lps ? num_lps : 1)));
     CU(cudaMemsetAsync(bt->x, 0, sizeof(double) * (size_t)n * num_lps, s));
@@ -434,44 +120,53 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
         CU(cudaStreamSynchronize(s));
         return LPB_OK;
     }
-    const int ce = h->opt.check_every;
-    if (h->opt.profile && (int)h->events.size() < 3 * ce + 3) {
-        for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-        h->events.assign(3 * ce + 3, nullptr);
-        for (auto& e : h->events) CU(cudaEventCreate(&e));
-    }
-    IterData<T> id = iter_data<T>(h);
-    IterBufs<T> ib = iter_bufs<T>(h);
-    CheckData cd = check_data(h, tol);
-    CU(launch_init<T>(cd, id, ib, ld, num_lps, specs_dev, wx, wy, h->c_norm_base, h->b_norm, h->rec, h->ctl, s));
+    GroupRun g;
+    g.id = 0;
+    g.count = num_lps;
+    g.slot0 = 0;
+    g.max_iter = max_iter;
+    g.res = bt->res.data();
+    g.x_dev = bt->x;
+    g.y_dev = bt->y;
+    std::vector<GroupRun*> groups(1, nullptr);
     prof.kernels += 3;
-    CU(cudaMemcpyAsync(h->rec_h, h->rec, sizeof(ColRecord) * num_lps, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (h->ctl_h->error) {
-        const int code = h->ctl_h->error;
-        return fail((lpb_err)code, code == LPB_ERR_BAD_INDEX ? "an override names a variable outside [0, n)"
-                                                              : "an override record has an invalid kind or value");
-    }
-    SolveState st;
-    st.colmap.resize(num_lps);
-    for (int j = 0; j < num_lps; ++j) st.colmap[j] = j;
-    st.ncol = num_lps;
-    std::vector<int> fin;
-    for (int j = 0; j < num_lps; ++j)
-        if (h->rec_h[j].status >= 0) {
-            set_result(bt->res[j], h->rec_h[j], h->rec_h[j].status, 0, 0);
-            fin.push_back(j);
-        }
-    if ((rc = compact<T>(h, st, fin, prof)) != LPB_OK) return rc;
-    if ((rc = run_phase<T>(h, st, tol, max_iter, bt)) != LPB_OK) return rc;
-    if (!st.done) {
-        // FP64 polish: the remaining batch continues from its FP32 state with
-        // FP64 iterates; the batch state on the device (k, r0, w, ...) carries over
-        CU(launch_promote(cd, iter_bufs<float>(h), iter_bufs<double>(h), iter_data<double>(h).col, ld, st.ncol, s));
+    rc = lane_admit<T>(h, ln, g, specs_dev, wx, wy, n, m, tol, s, groups);
+    bool done = true;
+    const bool can_stall = std::is_same<T, float>::value && polish_enabled(h);
+    if (rc == LPB_OK && g.live > 0) rc = run_group<T>(h, ln, g, groups, can_stall, done, prof);
+    if (rc == LPB_OK && !done) {
+        // polish: the group continues from its FP32 state in double-float (or
+        // FP64) iterates with its restart state (k, r0, w, ...) carried over
+        const int pp = polish_dfloat(h) ? kPrecDfl : kPrecF64;
+        Lane& pl = h->lane[pp];
+        std::vector<GroupRun*> pgroups(1, nullptr);
         prof.kernels += 5;
-        prof.fp64_switch_iter = st.K;
-        if ((rc = run_phase<double>(h, st, tol, max_iter, bt)) != LPB_OK) return rc;
+        prof.fp64_switch_iter = g.K;
+        if ((rc = lane_reserve(h, pl, pp, ln.cap, 1)) == LPB_OK) {
+            if (pp == kPrecDfl) {
+                if ((rc = lane_migrate<dfloat>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
+                    pgroups[0] = &g;
+                    rc = run_group<dfloat>(h, pl, g, pgroups, false, done, prof);
+                }
+            } else {
+                if ((rc = lane_migrate<double>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
+                    pgroups[0] = &g;
+                    rc = run_group<double>(h, pl, g, pgroups, false, done, prof);
+                }
+            }
+        }
+        if (rc != LPB_OK) {
+            pl.ncol = 0;
+            cudaMemsetAsync(pl.ctl, 0, sizeof(Control) * pl.gcap, s);
+        }
+    }
+    if (rc != LPB_OK) {
+        // leave the lane empty for the next solve
+        ln.ncol = 0;
+        std::fill(ln.slot_used.begin(), ln.slot_used.end(), 0);
+        cudaMemsetAsync(ln.ctl, 0, sizeof(Control) * ln.gcap, s);
+        cudaStreamSynchronize(s);
+        return rc;
     }
     CU(cudaStreamSynchronize(s));
     return LPB_OK;
@@ -532,6 +227,7 @@ void lpb_default_options(lpb_options* o) {
     o->device = -1;
     o->fp64_polish = 1;
     o->polish_stall_checks = 32;
+    o->polish_arith = LPB_POLISH_DFLOAT;
 }
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
@@ -555,7 +251,8 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
     lpb_default_options(&o);
     if (opt) o = *opt;
     if (o.precision != LPB_FP64 && o.precision != LPB_MIXED) return fail(LPB_ERR_INVALID_ARG, "bad precision");
-    if (o.check_every < 1 || o.ruiz_iters < 0 || o.power_max_iter < 1 || (o.fp64_polish && o.polish_stall_checks < 1) || !(o.power_tol >= 0.0) ||
+    if (o.check_every < 1 || o.ruiz_iters < 0 || o.power_max_iter < 1 || (o.fp64_polish && o.polish_stall_checks < 1) ||
+        (o.polish_arith != LPB_POLISH_DFLOAT && o.polish_arith != LPB_POLISH_FP64) || !(o.power_tol >= 0.0) ||
         !(o.theta >= 0.0 && o.theta <= 1.0) || !(o.beta_s >= 0.0) || !(o.beta_n >= 0.0) || !(o.beta_a >= 0.0))
         return fail(LPB_ERR_INVALID_ARG, "bad option value");
     // host validation, O(nnz)
@@ -703,6 +400,22 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
             CU(split_df(h->l, h->f_l, m, false, s));
             CU(split_df(h->u, h->f_u, m, false, s));
         }
+        if (polish_dfloat(h)) {
+            // the scaled data as dfloat pairs for a double-float polish phase
+            CU(dmalloc(F, &h->a_dfl, sizeof(dfloat) * nnz));
+            CU(dmalloc(F, &h->at_dfl, sizeof(dfloat) * nnz));
+            dfloat** nv[] = {&h->cs_dfl, &h->xls_dfl, &h->xus_dfl};
+            for (dfloat** p : nv) CU(dmalloc(F, p, sizeof(dfloat) * n));
+            dfloat** mv[] = {&h->ls_dfl, &h->us_dfl};
+            for (dfloat** p : mv) CU(dmalloc(F, p, sizeof(dfloat) * mm));
+            CU(split_df(h->A.v64, (df*)h->a_dfl, (int)nnz, false, s));
+            CU(split_df(h->At.v64, (df*)h->at_dfl, (int)nnz, false, s));
+            CU(split_df(h->cs, (df*)h->cs_dfl, n, false, s));
+            CU(split_df(h->xls, (df*)h->xls_dfl, n, false, s));
+            CU(split_df(h->xus, (df*)h->xus_dfl, n, false, s));
+            CU(split_df(h->ls, (df*)h->ls_dfl, m, false, s));
+            CU(split_df(h->us, (df*)h->us_dfl, m, false, s));
+        }
         // ||c~||, ||b~|| (w0) and the power iteration (eta)
         double* scal = nullptr;
         CU(dmalloc(tmp.v, &scal, sizeof(double) * 2));
@@ -751,7 +464,7 @@ lpb_err lpb_solve(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs, doubl
         if (sp.kind == 2 && !std::isfinite(sp.sign)) return fail(LPB_ERR_INVALID_ARG, "non-finite objective sign");
     }
     DeviceGuard guard(h->device);
-    if ((rc = ensure_workspace(h, num_lps)) != LPB_OK) return rc;
+    if ((rc = ensure_specs(h, num_lps)) != LPB_OK) return rc;
     cudaStream_t s = h->stream;
     double *wx = nullptr, *wy = nullptr;
     if (num_lps > 0) CU(cudaMemcpyAsync(h->specs_dev, specs, sizeof(lpb_lp_spec) * num_lps, cudaMemcpyHostToDevice, s));
@@ -838,7 +551,9 @@ void lpb_destroy(lpb_handle h) {
     DeviceGuard guard(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-    free_workspace(h);
+    for (auto& ln : h->lane) lane_free(ln);
+    free_list(h->ws_allocs);
+    if (h->specs_dev) cudaFree(h->specs_dev);
     free_list(h->fixed_allocs);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

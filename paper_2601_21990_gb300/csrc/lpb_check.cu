@@ -8,6 +8,8 @@
 //   batch (Sec. 5 "Stopping criteria and infeasibility detection").
 // Per-LP sums are reduced in a fixed order (per-block partials, then a
 // fixed tree), so a solve is bitwise reproducible.
+#include <type_traits>
+
 #include "lpb_internal.h"
 
 namespace lpb {
@@ -19,6 +21,7 @@ constexpr unsigned kFull = 0xffffffffu;
 template <typename T> struct Vec;
 template <> struct Vec<float> { static constexpr int V = 4; };
 template <> struct Vec<double> { static constexpr int V = 2; };
+template <> struct Vec<dfloat> { static constexpr int V = 2; };
 
 __device__ __forceinline__ void ldg_d(const float* p, double (&r)[4]) {
     float4 u = __ldg(reinterpret_cast<const float4*>(p));
@@ -297,16 +300,21 @@ __global__ void k_colsum(const double* __restrict__ part, int nb_m, int nb_n, in
 }
 
 // Halpern weights (k+1)/(k+2) and 1/(k+2) of Eq. mainiter for the
-// iterations k0 .. k0+ce-1 of the next interval, computed once in FP64 so
-// that the iteration kernels do no division.
-__device__ __forceinline__ void write_halpern(double* hal64, float* hal32, int k0, int ce) {
-    for (int t = threadIdx.x; t < ce; t += blockDim.x) {
+// iterations k0 .. k0+ce-1 of group g's next interval, computed once in FP64
+// so that the iteration kernels do no division; thread `me` of `nth` writes
+// every nth entry.
+__device__ __forceinline__ void write_halpern(double* hal64, float* hal32, dfloat* haldf, int g, int k0, int ce,
+                                              int me, int nth) {
+    for (int t = me; t < ce; t += nth) {
         const double k = (double)k0 + t;
         const double ca = (k + 1.0) / (k + 2.0), cb = 1.0 / (k + 2.0);
-        hal64[2 * t] = ca;
-        hal64[2 * t + 1] = cb;
-        hal32[2 * t] = (float)ca;
-        hal32[2 * t + 1] = (float)cb;
+        const size_t h = 2 * ((size_t)g * ce + t);
+        hal64[h] = ca;
+        hal64[h + 1] = cb;
+        hal32[h] = (float)ca;
+        hal32[h + 1] = (float)cb;
+        haldf[h] = dfloat(ca);
+        haldf[h + 1] = dfloat(cb);
     }
 }
 
@@ -316,30 +324,36 @@ struct DecideArgs {
     int ld, ncol;
     ColCheck col;
     ColParams<T> colp;
-    double eta, tol, eps_inf, mnorm_sign, beta_s, beta_n, beta_a, theta;
-    int detect_inf, interval_len, final_check, stall_checks;
-    long long k_eval_global;
+    double eta, mnorm_sign, beta_s, beta_n, beta_a, theta;
+    int detect_inf, interval_len, stall_checks, check_every;
     ColRecord* rec;
-    Control* ctl;
+    Control* ctl;     // gcap groups
+    int gcap;
     double* hal64;
     float* hal32;
-    int check_every;
+    dfloat* haldf;
+    double* rscr;     // residual of each active LP at this check, by slot
+    int* rtag;        // == tag where rscr holds this check's value
+    int tag;
+    int* flags;       // [0]: some group restarted
 };
 
 constexpr int kDecideThreads = 1024;
 
-// Per-LP status from the summed statistics, then the batch-averaged restart
-// test and, on a restart, the primal-weight update of every LP still active.
+// Per-LP status from the summed statistics; then, for each restart group,
+// the batch-averaged restart test (Sec. 5 "Restarts") over the group's
+// active LPs, summed in slot order by a fixed tree so that a group's result
+// does not depend on which columns its LPs occupy or what else runs beside
+// it; on a restart, the primal-weight update of the group's active LPs.
 template <typename T>
 __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a) {
-    __shared__ double sh_sum[kDecideThreads / 32];
-    __shared__ int sh_cnt[kDecideThreads / 32];
-    __shared__ int sh_stall[kDecideThreads / 32];
-    __shared__ int sh_restart;
-    double lsum = 0.0;
-    int lcnt = 0, lstall = 0;
     const size_t ld = (size_t)a.ld;
+    for (int g = threadIdx.x; g < a.gcap; g += blockDim.x) a.ctl[g].stalled = 0;
+    if (threadIdx.x == 0) a.flags[0] = 0;
+    __syncthreads();
     for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
+        const int g = a.col.grp[j];
+        const double tol = a.ctl[g].tol, eps_inf = a.ctl[g].eps_inf;
         double st[kNumStats];
         for (int s = 0; s < kNumStats; ++s) st[s] = a.colsum[s * ld + j];
         const double rel_p = sqrt(st[S_PRES2]) / (1.0 + sqrt(st[S_AX2]));
@@ -353,14 +367,14 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         int status = -1;
         if (isnan(ctx) || isnan(dsum) || isnan(rel_p) || isnan(rel_d) || isnan(rel_g) || !isfinite(r)) {
             status = LPB_NUMERICAL;
-        } else if (rel_p <= a.tol && rel_d <= a.tol && rel_g <= a.tol) {
+        } else if (rel_p <= tol && rel_d <= tol && rel_g <= tol) {
             status = LPB_OPTIMAL;
         } else if (a.detect_inf) {
             const double ph = st[S_PHIDY] + st[S_PHIDR];
             const double cdx = st[S_CDX];
-            if (ph < 0.0 && sqrt(st[S_RES2]) <= a.eps_inf * fabs(ph)) status = LPB_PRIMAL_INFEASIBLE;
-            else if (cdx < 0.0 && sqrt(st[S_RX2]) <= a.eps_inf * fabs(cdx) &&
-                     sqrt(st[S_RA2]) <= a.eps_inf * fabs(cdx))
+            if (ph < 0.0 && sqrt(st[S_RES2]) <= eps_inf * fabs(ph)) status = LPB_PRIMAL_INFEASIBLE;
+            else if (cdx < 0.0 && sqrt(st[S_RX2]) <= eps_inf * fabs(cdx) &&
+                     sqrt(st[S_RA2]) <= eps_inf * fabs(cdx))
                 status = LPB_DUAL_INFEASIBLE;
         }
         ColRecord rc;
@@ -374,8 +388,9 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         rc.rel_gap = rel_g;
         a.rec[j] = rc;
         if (status < 0) {
-            lsum += r;
-            ++lcnt;
+            const int slot = a.col.slot[j];
+            a.rscr[slot] = r;
+            a.rtag[slot] = a.tag;
             if (a.stall_checks > 0) {
                 // an LP stalls when its KKT error has not halved for stall_checks checks
                 const double err = fmax(rel_p, fmax(rel_d, rel_g));
@@ -383,63 +398,67 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
                     a.col.best[j] = err;
                     a.col.stall[j] = 0;
                 } else if (++a.col.stall[j] >= a.stall_checks) {
-                    lstall = 1;
+                    a.ctl[g].stalled = 1;
                 }
             }
         }
     }
-    // deterministic block sum
-    for (int o = 16; o > 0; o >>= 1) {
-        lsum += __shfl_down_sync(kFull, lsum, o);
-        lcnt += __shfl_down_sync(kFull, lcnt, o);
-        lstall |= __shfl_down_sync(kFull, lstall, o);
-    }
+    __syncthreads();
+    // one warp per group: the averaged residual and the restart test
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        sh_sum[warp] = lsum;
-        sh_cnt[warp] = lcnt;
-        sh_stall[warp] = lstall;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        int cnt = 0, stall = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            tot += sh_sum[q];
-            cnt += sh_cnt[q];
-            stall |= sh_stall[q];
-        }
-        Control* c = a.ctl;
-        c->stalled = stall;
-        int restart = 0;
-        double rt = cnt > 0 ? tot / cnt : 0.0;
-        if (cnt > 0 && !a.final_check) {
-            if (c->r0 < 0.0) {
-                c->r0 = rt;
-                c->r_prev = rt;
-            }
-            const long long k_eval = (long long)c->k + a.interval_len - 1;
-            restart = (rt <= a.beta_s * c->r0) || (rt <= a.beta_n * c->r0 && rt > c->r_prev) ||
-                      ((double)k_eval > a.beta_a * (double)a.k_eval_global);
-            if (restart) {
-                c->k = 0;
-                c->r0 = rt;
-                c->r_prev = rt;
-                c->restarts += 1;
-            } else {
-                c->k += a.interval_len;
-                c->r_prev = rt;
+    for (int g = warp; g < a.gcap; g += blockDim.x >> 5) {
+        Control* c = a.ctl + g;
+        if (!c->active) continue;
+        double sum = 0.0;
+        int cnt = 0;
+        for (int q = lane; q < c->nslots; q += 32) {
+            const int slot = c->slot0 + q;
+            if (a.rtag[slot] == a.tag) {
+                sum += a.rscr[slot];
+                ++cnt;
             }
         }
-        c->restart = restart;
-        c->r_avg = rt;
-        sh_restart = restart;
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_down_sync(kFull, sum, o);
+            cnt += __shfl_down_sync(kFull, cnt, o);
+        }
+        int k_next = 0;
+        if (lane == 0) {
+            const int L = a.interval_len;
+            const bool final_check = c->K + L >= c->max_iter;
+            int restart = 0;
+            const double rt = cnt > 0 ? sum / cnt : 0.0;
+            if (cnt > 0 && !final_check) {
+                if (c->r0 < 0.0) {
+                    c->r0 = rt;
+                    c->r_prev = rt;
+                }
+                const long long k_eval = (long long)c->k + L - 1;
+                const long long k_eval_global = (long long)c->K + L - 1;
+                restart = (rt <= a.beta_s * c->r0) || (rt <= a.beta_n * c->r0 && rt > c->r_prev) ||
+                          ((double)k_eval > a.beta_a * (double)k_eval_global);
+                if (restart) {
+                    c->k = 0;
+                    c->r0 = rt;
+                    c->r_prev = rt;
+                    c->restarts += 1;
+                    atomicOr(a.flags, 1);
+                } else {
+                    c->k += L;
+                    c->r_prev = rt;
+                }
+            }
+            c->K += L;
+            c->restart = restart;
+            c->r_avg = rt;
+            k_next = c->k;
+        }
+        k_next = __shfl_sync(kFull, k_next, 0);
+        write_halpern(a.hal64, a.hal32, a.haldf, g, k_next, a.check_every, lane, 32);
     }
     __syncthreads();
-    write_halpern(a.hal64, a.hal32, a.ctl->k, a.check_every);
-    if (!sh_restart) return;
     for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
-        if (a.rec[j].status >= 0) continue;
+        if (a.rec[j].status >= 0 || !a.ctl[a.col.grp[j]].restart) continue;
         const double ddx = a.colsum[S_DX02 * ld + j], ddy = a.colsum[S_DY02 * ld + j];
         const double d = sqrt(ddy) / sqrt(ddx);   // ||y^{n+1,0} - y^{n,0}|| / ||x^{n+1,0} - x^{n,0}||
         if (ddx > 0.0 && ddy > 0.0 && isfinite(d) && d > 0.0) {
@@ -451,16 +470,17 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
     }
 }
 
-// On a restart: anchor and iterate <- T(z) at the check (or the anchor <-
-// the Halpern iterate for restart_to_output = 0).
+// On a restart of a column's group: anchor and iterate <- T(z) at the check
+// (or the anchor <- the Halpern iterate for restart_to_output = 0).
 template <typename T>
 __global__ void k_restart_copy(T* __restrict__ Z, T* __restrict__ Z0, const T* __restrict__ Zh, int rows, int ld,
-                               int ncol, int to_output, const Control* __restrict__ ctl) {
-    if (!ctl->restart) return;
+                               int ncol, int to_output, const int* __restrict__ grp, const Control* __restrict__ ctl,
+                               const int* __restrict__ flags) {
+    if (!flags[0]) return;
     const size_t total = (size_t)rows * ld;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(p % ld);
-        if (j >= ncol) continue;
+        if (j >= ncol || !ctl[grp[j]].restart) continue;
         if (to_output) {
             const T v = Zh[p];
             Z[p] = v;
@@ -476,8 +496,10 @@ __global__ void k_restart_copy(T* __restrict__ Z, T* __restrict__ Z0, const T* _
 // ---------------------------------------------------------------------------
 template <typename T>
 struct InitArgs {
-    int m, n, ld, ncol;
-    const lpb_lp_spec* specs;
+    int m, n, ld;
+    int c0, count;                       // admitted columns [c0, c0 + count)
+    int group, slot0;                    // their restart group and first residual slot
+    const lpb_lp_spec* specs;            // count records
     const double *d_r, *d_c, *xl, *xu;   // original box
     const T *xls, *xus;                  // scaled box, iterate precision
     double eta, c_norm_base, b_norm;
@@ -487,62 +509,84 @@ struct InitArgs {
     Control* ctl;
 };
 
-// runs before k_init_columns, whose blocks may raise ctl->error
-__global__ void k_init_control(Control* ctl, double* hal64, float* hal32, int ce) {
+// A new restart group g owning residual slots [slot0, slot0 + nslots); runs
+// before k_init_columns, whose threads may raise ctl[g].error.
+__global__ void k_admit_group(Control* ctl, int g, int slot0, int nslots, double tol, double eps_inf,
+                              long long max_iter, double* hal64, float* hal32, dfloat* haldf, int ce) {
     if (threadIdx.x == 0) {
-        ctl->k = 0;
-        ctl->restart = 0;
-        ctl->error = 0;
-        ctl->stalled = 0;
-        ctl->r0 = -1.0;
-        ctl->r_prev = -1.0;
-        ctl->r_avg = 0.0;
-        ctl->restarts = 0;
+        Control c{};
+        c.k = 0;
+        c.restart = 0;
+        c.error = 0;
+        c.stalled = 0;
+        c.r0 = -1.0;
+        c.r_prev = -1.0;
+        c.r_avg = 0.0;
+        c.restarts = 0;
+        c.K = 0;
+        c.max_iter = max_iter;
+        c.tol = tol;
+        c.eps_inf = eps_inf;
+        c.slot0 = slot0;
+        c.nslots = nslots;
+        c.active = 1;
+        c.pad = 0;
+        ctl[g] = c;
     }
-    write_halpern(hal64, hal32, 0, ce);
+    write_halpern(hal64, hal32, haldf, g, 0, ce, threadIdx.x, blockDim.x);
+}
+
+// Group g now lives at ctl[g] of another lane (copied there by the host):
+// its slots move to slot0 and its Halpern table is written for its k.
+__global__ void k_group_moved(Control* ctl, int g, int slot0, double* hal64, float* hal32, dfloat* haldf, int ce) {
+    const int k = ctl[g].k;
+    __syncthreads();
+    if (threadIdx.x == 0) ctl[g].slot0 = slot0;
+    write_halpern(hal64, hal32, haldf, g, k, ce, threadIdx.x, blockDim.x);
 }
 
 template <typename T>
 __global__ void k_init_columns(const InitArgs<T> a) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.ld) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.count) return;
+    const int j = a.c0 + q;
+    Control* ctl = a.ctl + a.group;
     int kind = 0, var = -1;
     double olo = 0.0, ohi = 0.0, oc = 0.0;
     T slo = T(0), shi = T(0), sc = T(0);
     double cn = a.c_norm_base;
     int status = -1;
-    if (j < a.ncol) {
-        const lpb_lp_spec sp = a.specs[j];
-        kind = sp.kind;
-        var = sp.var;
-        if (kind < 0 || kind > 2) {
-            atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
-            kind = 0;
-        }
-        if (kind != 0 && (var < 0 || var >= a.n)) {
-            atomicMax(&a.ctl->error, (int)LPB_ERR_BAD_INDEX);
-            kind = 0;
-        }
-        if (kind == 0) var = -1;
-        if (kind == 1) {
-            olo = sp.lo > a.xl[var] ? sp.lo : a.xl[var];
-            ohi = sp.hi < a.xu[var] ? sp.hi : a.xu[var];
-            if (isnan(sp.lo) || isnan(sp.hi)) atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
-            if (olo > ohi) status = LPB_PRIMAL_INFEASIBLE;
-            slo = (T)(olo / a.d_c[var]);
-            shi = (T)(ohi / a.d_c[var]);
-        } else if (kind == 2) {
-            if (!isfinite(sp.sign)) atomicMax(&a.ctl->error, (int)LPB_ERR_INVALID_ARG);
-            oc = sp.sign;
-            sc = (T)(a.d_c[var] * sp.sign);
-            cn = fabs(a.d_c[var] * sp.sign);
-        }
+    const lpb_lp_spec sp = a.specs[q];
+    kind = sp.kind;
+    var = sp.var;
+    if (kind < 0 || kind > 2) {
+        atomicMax(&ctl->error, (int)LPB_ERR_INVALID_ARG);
+        kind = 0;
+    }
+    if (kind != 0 && (var < 0 || var >= a.n)) {
+        atomicMax(&ctl->error, (int)LPB_ERR_BAD_INDEX);
+        kind = 0;
+    }
+    if (kind == 0) var = -1;
+    if (kind == 1) {
+        olo = sp.lo > a.xl[var] ? sp.lo : a.xl[var];
+        ohi = sp.hi < a.xu[var] ? sp.hi : a.xu[var];
+        if (isnan(sp.lo) || isnan(sp.hi)) atomicMax(&ctl->error, (int)LPB_ERR_INVALID_ARG);
+        if (olo > ohi) status = LPB_PRIMAL_INFEASIBLE;
+        slo = (T)(olo / a.d_c[var]);
+        shi = (T)(ohi / a.d_c[var]);
+    } else if (kind == 2) {
+        if (!isfinite(sp.sign)) atomicMax(&ctl->error, (int)LPB_ERR_INVALID_ARG);
+        oc = sp.sign;
+        sc = (T)(a.d_c[var] * sp.sign);
+        cn = fabs(a.d_c[var] * sp.sign);
     }
     double w = 1.0;
     const double w0 = cn / a.b_norm;
     if (cn > 0.0 && a.b_norm > 0.0 && isfinite(w0)) w = w0;
     a.colp.kind[j] = kind;
     a.colp.var[j] = var;
+    a.colp.grp[j] = a.group;
     a.colp.lo[j] = slo;
     a.colp.hi[j] = shi;
     a.colp.c[j] = sc;
@@ -554,65 +598,69 @@ __global__ void k_init_columns(const InitArgs<T> a) {
     a.colc.hi[j] = ohi;
     a.colc.c[j] = oc;
     a.colc.w[j] = w;
-    a.colc.lp[j] = j;
+    a.colc.slot[j] = a.slot0 + q;
     a.colc.best[j] = INFINITY;
     a.colc.stall[j] = 0;
-    if (j < a.ncol) {
-        ColRecord rc;
-        rc.status = status;
-        rc.pad = 0;
-        rc.r = 0.0;
-        rc.obj = rc.dual_obj = rc.rel_primal = rc.rel_dual = rc.rel_gap = NAN;
-        a.rec[j] = rc;
-    }
+    ColRecord rc;
+    rc.status = status;
+    rc.pad = 0;
+    rc.r = 0.0;
+    rc.obj = rc.dual_obj = rc.rel_primal = rc.rel_dual = rc.rel_gap = NAN;
+    a.rec[j] = rc;
 }
 
-// z0 = (Pi_box(warm_x / D_c), warm_y / D_r), or (Pi_box(0), 0)
+// z0 = (Pi_box(warm_x / D_c), warm_y / D_r), or (Pi_box(0), 0), for the
+// admitted columns; LP q's warm start is warm_x + q * wsx (n values) and
+// warm_y + q * wsy (m values): column-major blocks, or one vector for every
+// LP with stride 0
 template <typename T>
 __global__ void k_init_iterates(const InitArgs<T> a, T* X, T* X0, T* Y, T* Y0, const double* warm_x,
-                                const double* warm_y) {
-    const size_t nx = (size_t)a.n * a.ld, ny = (size_t)a.m * a.ld;
+                                const double* warm_y, long long wsx, long long wsy) {
+    const size_t nx = (size_t)a.n * a.count, ny = (size_t)a.m * a.count;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < nx + ny; p += (size_t)gridDim.x * blockDim.x) {
         if (p < nx) {
-            const int i = (int)(p / a.ld), j = (int)(p % a.ld);
-            T v = T(0);
-            if (j < a.ncol) {
-                T lo = a.xls[i], hi = a.xus[i];
-                const int kind = a.colp.kind[j];
-                if (kind == 1 && a.colp.var[j] == i) { lo = a.colp.lo[j]; hi = a.colp.hi[j]; }
-                const T w = warm_x ? (T)(warm_x[(size_t)j * a.n + i] / a.d_c[i]) : T(0);
-                T t = w < hi ? w : hi;
-                v = t > lo ? t : lo;
-            }
-            X[p] = v;
-            X0[p] = v;
+            const int i = (int)(p / a.count), q = (int)(p % a.count);
+            const int j = a.c0 + q;
+            T lo = a.xls[i], hi = a.xus[i];
+            const int kind = a.colp.kind[j];
+            if (kind == 1 && a.colp.var[j] == i) { lo = a.colp.lo[j]; hi = a.colp.hi[j]; }
+            const T w = warm_x ? (T)(warm_x[q * wsx + i] / a.d_c[i]) : T(0);
+            T t = w < hi ? w : hi;
+            const T v = t > lo ? t : lo;
+            const size_t e = (size_t)i * a.ld + j;
+            X[e] = v;
+            X0[e] = v;
         } else {
-            const size_t q = p - nx;
-            const int i = (int)(q / a.ld), j = (int)(q % a.ld);
-            T v = T(0);
-            if (j < a.ncol && warm_y) v = (T)(warm_y[(size_t)j * a.m + i] / a.d_r[i]);
-            Y[q] = v;
-            Y0[q] = v;
+            const size_t r = p - nx;
+            const int i = (int)(r / a.count), q = (int)(r % a.count);
+            const T v = warm_y ? (T)(warm_y[q * wsy + i] / a.d_r[i]) : T(0);
+            const size_t e = (size_t)i * a.ld + a.c0 + q;
+            Y[e] = v;
+            Y0[e] = v;
         }
     }
 }
 
+// finished column cols[f] -> x at outp[f] (n) and y at outp[count + f] (m),
+// in the original space
 template <typename T>
-__global__ void k_extract(int n, int m, int ld, const int* __restrict__ cols, const int* __restrict__ lps, int count,
-                          const double* __restrict__ d_r, const double* __restrict__ d_c, const double* __restrict__ xl,
-                          const double* __restrict__ xu, ColCheck colc, const T* __restrict__ Xh,
-                          const T* __restrict__ Yh, double* __restrict__ x_out, double* __restrict__ y_out) {
+__global__ void k_extract(int n, int m, int ld, const int* __restrict__ cols, double* const* __restrict__ outp,
+                          int count, const double* __restrict__ d_r, const double* __restrict__ d_c,
+                          const double* __restrict__ xl, const double* __restrict__ xu, ColCheck colc,
+                          const T* __restrict__ Xh, const T* __restrict__ Yh) {
     const int f = blockIdx.y;
     if (f >= count) return;
-    const int j = cols[f], lp = lps[f];
+    const int j = cols[f];
+    double* x_out = outp[f];
+    double* y_out = outp[count + f];
     const int kind = colc.kind[j], var = colc.var[j];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n > m ? n : m); i += gridDim.x * blockDim.x) {
-        if (i < n) {
+        if (i < n && x_out) {
             double lo = xl[i], hi = xu[i];
             if (kind == 1 && var == i) { lo = colc.lo[j]; hi = colc.hi[j]; }
-            x_out[(size_t)lp * n + i] = proj_box(d_c[i] * (double)Xh[(size_t)i * ld + j], lo, hi);
+            x_out[i] = proj_box(d_c[i] * (double)Xh[(size_t)i * ld + j], lo, hi);
         }
-        if (i < m) y_out[(size_t)lp * m + i] = d_r[i] * (double)Yh[(size_t)i * ld + j];
+        if (i < m && y_out) y_out[i] = d_r[i] * (double)Yh[(size_t)i * ld + j];
     }
 }
 
@@ -645,18 +693,17 @@ __global__ void k_compact_cols(ColParams<T> cp, ColCheck cc, const int* __restri
     const int s = src[p], d = dst[p];
     cp.kind[d] = cp.kind[s];
     cp.var[d] = cp.var[s];
+    cp.grp[d] = cp.grp[s];
     cp.lo[d] = cp.lo[s];
     cp.hi[d] = cp.hi[s];
     cp.c[d] = cp.c[s];
     cp.tau[d] = cp.tau[s];
     cp.sigma[d] = cp.sigma[s];
-    cc.kind[d] = cc.kind[s];
-    cc.var[d] = cc.var[s];
     cc.lo[d] = cc.lo[s];
     cc.hi[d] = cc.hi[s];
     cc.c[d] = cc.c[s];
     cc.w[d] = cc.w[s];
-    cc.lp[d] = cc.lp[s];
+    cc.slot[d] = cc.slot[s];
     cc.best[d] = cc.best[s];
     cc.stall[d] = cc.stall[s];
 }
@@ -669,9 +716,27 @@ inline int blocks_for(size_t work, int threads, int cap = 8192) {
 }
 
 // ---------------------------------------------------------------------------
-// double-float checks for FP32 iterates.  The FP64 versions above run for
-// FP64 iterates; these give FP64-level accuracy on the FP32 pipe.
+// double-float checks for FP32 and dfloat iterates.  The FP64 versions above
+// run for FP64 iterates; these give FP64-level accuracy on the FP32 pipe.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void ldg_it(const float* p, float (&r)[4]) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = u.x; r[1] = u.y; r[2] = u.z; r[3] = u.w;
+}
+__device__ __forceinline__ void ldg_it(const dfloat* p, dfloat (&r)[2]) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = dfloat(u.x, u.y); r[1] = dfloat(u.z, u.w);
+}
+// an iterate value as FP32 (norms) and as df (terms that cancel)
+__device__ __forceinline__ float it_f(float v) { return v; }
+__device__ __forceinline__ float it_f(dfloat v) { return v.hi + v.lo; }
+__device__ __forceinline__ df it_mul(df a, float v) { return df_mulf(a, v); }
+__device__ __forceinline__ df it_mul(df a, dfloat v) { return df_mul(a, df_of(v)); }
+// a - b rounded to FP32 (exact leading parts by Sterbenz when close)
+__device__ __forceinline__ float it_diff(float a, float b) { return a - b; }
+__device__ __forceinline__ float it_diff(dfloat a, dfloat b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+template <typename TI>
 struct SpmmDfArgs {
     int rows;
     const int* rp;
@@ -680,9 +745,9 @@ struct SpmmDfArgs {
     const float* vlo;
     const int* long_rows;
     int n_long;
-    const float* s0;
-    const float* s1;
-    const float* s2;
+    const TI* s0;
+    const TI* s1;
+    const TI* s2;
     df* o0;
     df* o1;
     df* o2;
@@ -690,9 +755,9 @@ struct SpmmDfArgs {
 };
 
 // o_q = A~ s_q for NOPS operands, each product a_e * x accumulated exactly
-template <int G, int NOPS>
-__global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs a) {
-    constexpr int V = 4, GPB = kBlock / G, TN = G * V;
+template <typename TI, int G, int NOPS>
+__global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs<TI> a) {
+    constexpr int V = Vec<TI>::V, GPB = kBlock / G, TN = G * V;
     __shared__ df red[NOPS * kBlock * V];
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
     const int col0 = blockIdx.y * TN + lane * V;
@@ -713,7 +778,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs a) {
     for (int q = 0; q < NOPS; ++q)
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[q][v] = df_zero();
-    const float* src[3] = {a.s0, a.s1, a.s2};
+    const TI* src[3] = {a.s0, a.s1, a.s2};
     if (active) {
         const int end = a.rp[row + 1];
         for (int e = a.rp[row] + slot; e < end; e += nslot) {
@@ -721,11 +786,10 @@ __global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs a) {
             const df w = df{a.vhi[e], a.vlo[e]};
 #pragma unroll
             for (int q = 0; q < NOPS; ++q) {
-                const float4 x = __ldg(reinterpret_cast<const float4*>(src[q] + (size_t)c * a.ld + col0));
-                df_fma_acc(acc[q][0], w, x.x);
-                df_fma_acc(acc[q][1], w, x.y);
-                df_fma_acc(acc[q][2], w, x.z);
-                df_fma_acc(acc[q][3], w, x.w);
+                TI x[V];
+                ldg_it(src[q] + (size_t)c * a.ld + col0, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) df_fma_acc(acc[q][v], w, x[v]);
             }
         }
     }
@@ -752,27 +816,29 @@ __global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs a) {
 #pragma unroll
     for (int q = 0; q < NOPS; ++q) {
         float4* p = reinterpret_cast<float4*>(out[q] + off);
-        p[0] = make_float4(acc[q][0].hi, acc[q][0].lo, acc[q][1].hi, acc[q][1].lo);
-        p[1] = make_float4(acc[q][2].hi, acc[q][2].lo, acc[q][3].hi, acc[q][3].lo);
+#pragma unroll
+        for (int v = 0; v < V; v += 2)
+            p[v / 2] = make_float4(acc[q][v].hi, acc[q][v].lo, acc[q][v + 1].hi, acc[q][v + 1].lo);
     }
 }
 
-template <int NOPS>
-cudaError_t spmm_df(const Csr& m, const float* s0, const float* s1, const float* s2, df* o0, df* o1, df* o2, int ld,
+template <typename TI, int NOPS>
+cudaError_t spmm_df(const Csr& m, const TI* s0, const TI* s1, const TI* s2, df* o0, df* o1, df* o2, int ld,
                     int ncol, cudaStream_t s) {
     if (m.rows == 0 || ncol == 0) return cudaSuccess;
-    SpmmDfArgs a{m.rows, m.rp, m.ci, m.v32, m.v32lo, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
-    const int vecs = (ncol + 3) / 4;
+    constexpr int V = Vec<TI>::V;
+    SpmmDfArgs<TI> a{m.rows, m.rp, m.ci, m.v32, m.v32lo, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
+    const int vecs = (ncol + V - 1) / V;
     const int G = vecs <= 1 ? 1 : vecs <= 2 ? 2 : vecs <= 4 ? 4 : vecs <= 8 ? 8 : vecs <= 16 ? 16 : 32;
-    const int gpb = kBlock / G, tn = G * 4;
+    const int gpb = kBlock / G, tn = G * V;
     dim3 grid(a.n_long + (a.rows + gpb - 1) / gpb, (ncol + tn - 1) / tn);
     switch (G) {
-        case 1: k_spmm_df<1, NOPS><<<grid, kBlock, 0, s>>>(a); break;
-        case 2: k_spmm_df<2, NOPS><<<grid, kBlock, 0, s>>>(a); break;
-        case 4: k_spmm_df<4, NOPS><<<grid, kBlock, 0, s>>>(a); break;
-        case 8: k_spmm_df<8, NOPS><<<grid, kBlock, 0, s>>>(a); break;
-        case 16: k_spmm_df<16, NOPS><<<grid, kBlock, 0, s>>>(a); break;
-        default: k_spmm_df<32, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 1: k_spmm_df<TI, 1, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 2: k_spmm_df<TI, 2, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 4: k_spmm_df<TI, 4, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 8: k_spmm_df<TI, 8, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        case 16: k_spmm_df<TI, 16, NOPS><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_spmm_df<TI, 32, NOPS><<<grid, kBlock, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -790,11 +856,12 @@ __device__ __forceinline__ df df_from(double v) {
     return df{hi, isfinite(v) && isfinite(hi) ? (float)(v - (double)hi) : 0.0f};
 }
 
+template <typename TI>
 struct ReduceDfArgs {
     int m, n, ld, ncol;
     const df *dr, *dc, *idr, *idc, *c, *xl, *xu, *l, *u;
     ColCheck col;
-    const float *Xh, *DX, *X0, *X, *Yh, *DY, *DYp, *Y0, *Y;
+    const TI *Xh, *DX, *X0, *X, *Yh, *DY, *DYp, *Y0, *Y;
     const df *P0, *P1, *Q0, *Q1, *Q2;
     double* part;
     int restart_to_output;
@@ -802,7 +869,8 @@ struct ReduceDfArgs {
 
 // m-side statistics (the same quantities as k_reduce_rows_m); the terms that
 // cancel (A x against its bounds, phi sums) in double-float, norms in FP32
-__global__ void k_reduce_m_df(const ReduceDfArgs a) {
+template <typename TI>
+__global__ void k_reduce_m_df(const ReduceDfArgs<TI> a) {
     const int j = blockIdx.y * 32 + threadIdx.x;
     const bool ok = j < a.ncol;
     float f_pres2 = 0.f, f_ax2 = 0.f, f_dy2 = 0.f, f_cross = 0.f, f_dy02 = 0.f, f_ra2 = 0.f;
@@ -815,16 +883,15 @@ __global__ void k_reduce_m_df(const ReduceDfArgs a) {
             const float pv = df_f(df_sub(ax, df_clamp(ax, l, u)));
             f_pres2 += pv * pv;
             f_ax2 += ax.hi * ax.hi;
-            const float yh = a.Yh[off];
-            df_acc(d_phy, df_support(df_mulf(dr, yh), l, u));         // phi_[l,u](y), y = D_r y~
-            const float dy = a.DY[off];
+            const TI yh = a.Yh[off];
+            df_acc(d_phy, df_support(it_mul(dr, yh), l, u));          // phi_[l,u](y), y = D_r y~
+            const float dy = it_f(a.DY[off]);
             f_dy2 += dy * dy;
             const float p1 = df_f(a.P1[off]);
             f_cross += dy * p1;                                      // <dy~, A~ dx~>
-            const float anchor = a.restart_to_output ? yh : a.Y[off];
-            const float dy0 = anchor - a.Y0[off];
+            const float dy0 = it_diff(a.restart_to_output ? yh : a.Y[off], a.Y0[off]);
             f_dy02 += dy0 * dy0;
-            df_acc(d_phidy, df_support(df_mulf(dr, a.DYp[off]), l, u));
+            df_acc(d_phidy, df_support(it_mul(dr, a.DYp[off]), l, u));
             const float adx = df_f(df_mulf(idr, p1));                // A dx, dx = D_c dx~
             const float t = adx - proj_recession_f(adx, l.hi, u.hi);
             f_ra2 += t * t;
@@ -834,7 +901,8 @@ __global__ void k_reduce_m_df(const ReduceDfArgs a) {
     write_partials<8>(s, a.part, S_PRES2, kReduceBlocks, a.ld, j, ok);
 }
 
-__global__ void k_reduce_n_df(const ReduceDfArgs a) {
+template <typename TI>
+__global__ void k_reduce_n_df(const ReduceDfArgs<TI> a) {
     const int j = blockIdx.y * 32 + threadIdx.x;
     const bool ok = j < a.ncol;
     float f_dres2 = 0.f, f_c2 = 0.f, f_dx2 = 0.f, f_dx02 = 0.f, f_res2 = 0.f, f_rx2 = 0.f;
@@ -848,8 +916,8 @@ __global__ void k_reduce_n_df(const ReduceDfArgs a) {
             df cj = a.c[i], lo = a.xl[i], hi = a.xu[i];
             if (kind == 2) cj = var == i ? oc : df_zero();
             else if (kind == 1 && var == i) { lo = olo; hi = ohi; }
-            const float xh = a.Xh[off];
-            const df x = df_clamp(df_mulf(dc, xh), lo, hi);
+            const TI xh = a.Xh[off];
+            const df x = df_clamp(it_mul(dc, xh), lo, hi);
             const df q = df_add(cj, df_mul(a.Q0[off], idc));         // c + A^T y
             const df r = df_barrier(df_neg(q), lo, hi);              // reduced cost
             const float d = df_f(df_add(q, r));
@@ -857,10 +925,10 @@ __global__ void k_reduce_n_df(const ReduceDfArgs a) {
             f_c2 += cj.hi * cj.hi;
             df_acc(d_ctx, df_mul(cj, x));
             df_acc(d_phr, df_support(r, lo, hi));
-            const float dx = a.DX[off];
-            f_dx2 += dx * dx;
-            const float anchor = a.restart_to_output ? xh : a.X[off];
-            const float dx0 = anchor - a.X0[off];
+            const TI dx = a.DX[off];
+            const float dxs = it_f(dx);
+            f_dx2 += dxs * dxs;
+            const float dx0 = it_diff(a.restart_to_output ? xh : a.X[off], a.X0[off]);
             f_dx02 += dx0 * dx0;
             // A^T y^k = A^T y^ - A^T (y^ - y^k)
             const df gk = df_mul(df_sub(a.Q0[off], a.Q2[off]), idc);
@@ -869,7 +937,7 @@ __global__ void k_reduce_n_df(const ReduceDfArgs a) {
             df_acc(d_phidr, df_support(drr, lo, hi));
             const float t = df_f(df_add(df_mul(a.Q1[off], idc), drr)); // A^T dy + dr
             f_res2 += t * t;
-            const df dxo = df_mulf(dc, dx);
+            const df dxo = it_mul(dc, dx);
             df_acc(d_cdx, df_mul(cj, dxo));
             const float dxf = df_f(dxo);
             const float t2 = dxf - proj_recession_f(dxf, lo.hi, hi.hi);
@@ -883,9 +951,9 @@ __global__ void k_reduce_n_df(const ReduceDfArgs a) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int64_t k_eval_global,
-                         int interval_len, bool final_check, double* P, double* Q, double* partials, double* colsum,
-                         ColRecord* rec, Control* ctl, ColParams<T> colp, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len, int tag,
+                         double* P, double* Q, double* partials, double* colsum, ColRecord* rec, ColParams<T> colp,
+                         cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
     const int m = d.m, n = d.n;
     double* P0 = P;
@@ -893,16 +961,14 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     double* Q0 = Q;
     double* Q1 = Q + (size_t)n * ld;
     double* Q2 = Q + 2 * (size_t)n * ld;
-    constexpr bool kDf = sizeof(T) == sizeof(float);
+    constexpr bool kDf = !std::is_same<T, double>::value;  // FP32 or dfloat iterates
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     // A~ [x^, x^ - x] and A~^T [y^, Pi_B(y^ - y), y^ - y]: in double-float for
     // FP32 iterates, in FP64 for FP64 iterates (P and Q hold either)
     if constexpr (kDf) {
-        if ((e = spmm_df<2>(d.A, (const float*)b.Xh, (const float*)b.DX, nullptr, (df*)P0, (df*)P1, nullptr, ld,
-                            ncol, s)) != cudaSuccess)
+        if ((e = spmm_df<T, 2>(d.A, b.Xh, b.DX, nullptr, (df*)P0, (df*)P1, nullptr, ld, ncol, s)) != cudaSuccess)
             return e;
-        if ((e = spmm_df<3>(d.At, (const float*)b.Yh, (const float*)b.DYp, (const float*)b.DY, (df*)Q0, (df*)Q1,
-                            (df*)Q2, ld, ncol, s)) != cudaSuccess)
+        if ((e = spmm_df<T, 3>(d.At, b.Yh, b.DYp, b.DY, (df*)Q0, (df*)Q1, (df*)Q2, ld, ncol, s)) != cudaSuccess)
             return e;
     } else {
         if ((e = spmm64<T, 2>(d.A, b.Xh, b.DX, nullptr, P0, P1, nullptr, ld, ncol, s)) != cudaSuccess) return e;
@@ -947,7 +1013,7 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     ra.restart_to_output = d.restart_to_output;
     const dim3 rblock(32, kReduceRows);
     if constexpr (kDf) {
-        ReduceDfArgs rd{};
+        ReduceDfArgs<T> rd{};
         rd.m = m;
         rd.n = n;
         rd.ld = ld;
@@ -962,15 +1028,15 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
         rd.l = d.f_l;
         rd.u = d.f_u;
         rd.col = d.col;
-        rd.Xh = (const float*)b.Xh;
-        rd.DX = (const float*)b.DX;
-        rd.X0 = (const float*)b.X0;
-        rd.X = (const float*)b.X;
-        rd.Yh = (const float*)b.Yh;
-        rd.DY = (const float*)b.DY;
-        rd.DYp = (const float*)b.DYp;
-        rd.Y0 = (const float*)b.Y0;
-        rd.Y = (const float*)b.Y;
+        rd.Xh = b.Xh;
+        rd.DX = b.DX;
+        rd.X0 = b.X0;
+        rd.X = b.X;
+        rd.Yh = b.Yh;
+        rd.DY = b.DY;
+        rd.DYp = b.DYp;
+        rd.Y0 = b.Y0;
+        rd.Y = b.Y;
         rd.P0 = (const df*)P0;
         rd.P1 = (const df*)P1;
         rd.Q0 = (const df*)Q0;
@@ -979,10 +1045,10 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
         rd.part = partials;
         rd.restart_to_output = d.restart_to_output;
         if (nb_m > 0) {
-            k_reduce_m_df<<<dim3(nb_m, tiles), rblock, 0, s>>>(rd);
+            k_reduce_m_df<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(rd);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        k_reduce_n_df<<<dim3(nb_n, tiles), rblock, 0, s>>>(rd);
+        k_reduce_n_df<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(rd);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         if (nb_m > 0) {
@@ -1002,8 +1068,6 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     da.col = d.col;
     da.colp = colp;
     da.eta = d.eta;
-    da.tol = d.tol;
-    da.eps_inf = d.eps_inf;
     da.mnorm_sign = d.mnorm_sign;
     da.beta_s = d.beta_s;
     da.beta_n = d.beta_n;
@@ -1012,34 +1076,43 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     da.detect_inf = d.detect_inf;
     da.stall_checks = d.stall_checks;
     da.interval_len = interval_len;
-    da.final_check = final_check ? 1 : 0;
-    da.k_eval_global = (long long)k_eval_global;
+    da.check_every = d.check_every;
     da.rec = rec;
-    da.ctl = ctl;
+    da.ctl = d.ctl;
+    da.gcap = d.gcap;
     da.hal64 = d.hal64;
     da.hal32 = d.hal32;
-    da.check_every = d.check_every;
+    da.haldf = d.haldf;
+    da.rscr = d.rscr;
+    da.rtag = d.rtag;
+    da.tag = tag;
+    da.flags = d.flags;
     k_decide<T><<<1, kDecideThreads, 0, s>>>(da);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_restart_copy<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.X0, b.Xh, n, ld, ncol,
-                                                                      d.restart_to_output, ctl);
+                                                                      d.restart_to_output, d.col.grp, d.ctl, d.flags);
     if (m > 0)
         k_restart_copy<T><<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(b.Y, b.Y0, b.Yh, m, ld, ncol,
-                                                                          d.restart_to_output, ctl);
+                                                                          d.restart_to_output, d.col.grp, d.ctl,
+                                                                          d.flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int ncol,
-                        const lpb_lp_spec* specs_dev, const double* warm_x, const double* warm_y, double c_norm_base,
-                        double b_norm, ColRecord* rec, Control* ctl, cudaStream_t s) {
+cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int c0, int count,
+                         int group, int slot0, const lpb_lp_spec* specs_dev, const double* warm_x,
+                         const double* warm_y, int64_t wsx, int64_t wsy, double c_norm_base, double b_norm,
+                         double tol, double eps_inf, int64_t max_iter, ColRecord* rec, cudaStream_t s) {
     InitArgs<T> a{};
     a.m = d.m;
     a.n = d.n;
     a.ld = ld;
-    a.ncol = ncol;
+    a.c0 = c0;
+    a.count = count;
+    a.group = group;
+    a.slot0 = slot0;
     a.specs = specs_dev;
     a.d_r = d.d_r;
     a.d_c = d.d_c;
@@ -1053,25 +1126,27 @@ cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBuf
     a.colp = it.col;
     a.colc = d.col;
     a.rec = rec;
-    a.ctl = ctl;
-    k_init_control<<<1, 256, 0, s>>>(ctl, d.hal64, d.hal32, d.check_every);
-    k_init_columns<T><<<(ld + 255) / 256, 256, 0, s>>>(a);
+    a.ctl = d.ctl;
+    k_admit_group<<<1, 256, 0, s>>>(d.ctl, group, slot0, count, tol, eps_inf, (long long)max_iter, d.hal64, d.hal32,
+                                    d.haldf, d.check_every);
+    if (count <= 0) return cudaGetLastError();
+    k_init_columns<T><<<(count + 255) / 256, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_init_iterates<T><<<blocks_for((size_t)(d.n + d.m) * ld, 256), 256, 0, s>>>(a, b.X, b.X0, b.Y, b.Y0, warm_x,
-                                                                                 warm_y);
+    k_init_iterates<T><<<blocks_for((size_t)(d.n + d.m) * count, 256), 256, 0, s>>>(a, b.X, b.X0, b.Y, b.Y0, warm_x,
+                                                                                    warm_y, wsx, wsy);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev, const int* lps_dev,
-                           int count, const double* xl_base, const double* xu_base, double* x_out, double* y_out,
+cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev,
+                           double* const* outp_dev, int count, const double* xl_base, const double* xu_base,
                            cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int rows = d.n > d.m ? d.n : d.m;
     dim3 grid(blocks_for(rows, 256, 1024), count);
-    k_extract<T><<<grid, 256, 0, s>>>(d.n, d.m, ld, cols_dev, lps_dev, count, d.d_r, d.d_c, xl_base, xu_base, d.col,
-                                      b.Xh, b.Yh, x_out, y_out);
+    k_extract<T><<<grid, 256, 0, s>>>(d.n, d.m, ld, cols_dev, outp_dev, count, d.d_r, d.d_c, xl_base, xu_base, d.col,
+                                      b.Xh, b.Yh);
     return cudaGetLastError();
 }
 
@@ -1087,61 +1162,102 @@ cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int
 
 namespace {
 
-__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, int rows, int ld, int ncol) {
-    const size_t total = (size_t)rows * ld;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
-        if ((int)(p % ld) < ncol) dst[p] = (double)src[p];
+// state of column sc of the FP32 lane -> column dc of the polish lane
+template <typename TD>
+__global__ void k_migrate_rows(const float* __restrict__ X, const float* __restrict__ X0,
+                               const float* __restrict__ Y, const float* __restrict__ Y0, TD* __restrict__ DXs,
+                               TD* __restrict__ DX0, TD* __restrict__ DY, TD* __restrict__ DY0, int n, int m,
+                               int lds, int ldd, const int* __restrict__ sc, const int* __restrict__ dc, int count) {
+    const size_t total = (size_t)(n + m) * count;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int mv = (int)(p % count);
+        const int row = (int)(p / count);
+        if (row < n) {
+            const size_t a = (size_t)row * lds + sc[mv], b = (size_t)row * ldd + dc[mv];
+            DXs[b] = TD(X[a]);
+            DX0[b] = TD(X0[a]);
+        } else {
+            const size_t a = (size_t)(row - n) * lds + sc[mv], b = (size_t)(row - n) * ldd + dc[mv];
+            DY[b] = TD(Y[a]);
+            DY0[b] = TD(Y0[a]);
+        }
+    }
 }
 
-// FP64 per-column parameters from the FP64 originals: the same formulas as
-// k_init_columns, with the current primal weight
-__global__ void k_colparams64(ColCheck cc, ColParams<double> cp, const double* __restrict__ d_c, double eta,
-                              int ld) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ld) return;
-    const int kind = cc.kind[j], var = cc.var[j];
+// per-column data of the moved columns; the polish-precision parameters
+// from the FP64 originals with the same formulas as k_init_columns and the
+// column's current primal weight
+template <typename TD>
+__global__ void k_migrate_cols(ColCheck src, ColCheck dst, ColParams<TD> cp, const int* __restrict__ sc,
+                               const int* __restrict__ dc, int count, int group, int slot_shift,
+                               const double* __restrict__ d_c, double eta) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count) return;
+    const int s = sc[p], j = dc[p];
+    const int kind = src.kind[s], var = src.var[s];
+    const double w = src.w[s];
+    dst.kind[j] = kind;
+    dst.var[j] = var;
+    dst.grp[j] = group;
+    dst.lo[j] = src.lo[s];
+    dst.hi[j] = src.hi[s];
+    dst.c[j] = src.c[s];
+    dst.w[j] = w;
+    dst.slot[j] = src.slot[s] + slot_shift;
+    dst.best[j] = src.best[s];
+    dst.stall[j] = 0;
     double lo = 0.0, hi = 0.0, c = 0.0;
     if (kind == 1) {
-        lo = cc.lo[j] / d_c[var];
-        hi = cc.hi[j] / d_c[var];
+        lo = src.lo[s] / d_c[var];
+        hi = src.hi[s] / d_c[var];
     } else if (kind == 2) {
-        c = d_c[var] * cc.c[j];
+        c = d_c[var] * src.c[s];
     }
-    cp.lo[j] = lo;
-    cp.hi[j] = hi;
-    cp.c[j] = c;
-    cp.tau[j] = eta / cc.w[j];
-    cp.sigma[j] = eta * cc.w[j];
-    cc.stall[j] = 0;
+    cp.lo[j] = TD(lo);
+    cp.hi[j] = TD(hi);
+    cp.c[j] = TD(c);
+    cp.tau[j] = TD(eta / w);
+    cp.sigma[j] = TD(eta * w);
 }
 
 }  // namespace
 
-cudaError_t launch_promote(const CheckData& d, const IterBufs<float>& src, const IterBufs<double>& dst,
-                           ColParams<double> colp64, int ld, int ncol, cudaStream_t s) {
-    const int n = d.n, m = d.m;
-    k_widen<<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(src.X, dst.X, n, ld, ncol);
-    k_widen<<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(src.X0, dst.X0, n, ld, ncol);
-    if (m > 0) {
-        k_widen<<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(src.Y, dst.Y, m, ld, ncol);
-        k_widen<<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(src.Y0, dst.Y0, m, ld, ncol);
-    }
-    k_colparams64<<<(ld + 255) / 256, 256, 0, s>>>(d.col, colp64, d.d_c, d.eta, ld);
+template <typename TD>
+cudaError_t launch_migrate(const CheckData& src, const IterBufs<float>& sb, int lds, const CheckData& dst,
+                           const IterBufs<TD>& db, int ldd, ColParams<TD> dcolp, const int* sc_dev, const int* dc_dev,
+                           int count, int group_dst, int slot_shift, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int n = src.n, m = src.m;
+    k_migrate_rows<TD><<<blocks_for((size_t)(n + m) * count, 256), 256, 0, s>>>(
+        sb.X, sb.X0, sb.Y, sb.Y0, db.X, db.X0, db.Y, db.Y0, n, m, lds, ldd, sc_dev, dc_dev, count);
+    k_migrate_cols<TD><<<(count + 255) / 256, 256, 0, s>>>(src.col, dst.col, dcolp, sc_dev, dc_dev, count, group_dst,
+                                                           slot_shift, src.d_c, src.eta);
+    return cudaGetLastError();
+}
+template cudaError_t launch_migrate<double>(const CheckData&, const IterBufs<float>&, int, const CheckData&,
+                                            const IterBufs<double>&, int, ColParams<double>, const int*, const int*,
+                                            int, int, int, cudaStream_t);
+template cudaError_t launch_migrate<dfloat>(const CheckData&, const IterBufs<float>&, int, const CheckData&,
+                                            const IterBufs<dfloat>&, int, ColParams<dfloat>, const int*, const int*,
+                                            int, int, int, cudaStream_t);
+
+cudaError_t launch_group_moved(const CheckData& dst, int group, int slot0, cudaStream_t s) {
+    k_group_moved<<<1, 256, 0, s>>>(dst.ctl, group, slot0, dst.hal64, dst.hal32, dst.haldf, dst.check_every);
     return cudaGetLastError();
 }
 
 #define LPB_INSTANTIATE(T)                                                                                        \
-    template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int64_t, int, bool, double*, \
-                                         double*, double*, double*, ColRecord*, Control*, ColParams<T>, cudaStream_t, \
-                                         cudaEvent_t*);                                                               \
-    template cudaError_t launch_init<T>(const CheckData&, const IterData<T>&, const IterBufs<T>&, int, int,           \
-                                        const lpb_lp_spec*, const double*, const double*, double, double,             \
-                                        ColRecord*, Control*, cudaStream_t);                                          \
-    template cudaError_t launch_extract<T>(const CheckData&, const IterBufs<T>&, int, const int*, const int*, int,    \
-                                           const double*, const double*, double*, double*, cudaStream_t);             \
+    template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int, int, double*, double*,  \
+                                         double*, double*, ColRecord*, ColParams<T>, cudaStream_t, cudaEvent_t*);     \
+    template cudaError_t launch_admit<T>(const CheckData&, const IterData<T>&, const IterBufs<T>&, int, int, int,     \
+                                         int, int, const lpb_lp_spec*, const double*, const double*, int64_t,         \
+                                         int64_t, double, double, double, double, int64_t, ColRecord*, cudaStream_t); \
+    template cudaError_t launch_extract<T>(const CheckData&, const IterBufs<T>&, int, const int*, double* const*,     \
+                                           int, const double*, const double*, cudaStream_t);                          \
     template cudaError_t launch_compact<T>(const IterBufs<T>&, int, int, int, const int*, const int*, int,            \
                                            ColParams<T>, ColCheck, cudaStream_t);
 LPB_INSTANTIATE(float)
 LPB_INSTANTIATE(double)
+LPB_INSTANTIATE(dfloat)
 
 }  // namespace lpb

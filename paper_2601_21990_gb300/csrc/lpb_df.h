@@ -110,4 +110,63 @@ LPB_HD df df_support(df v, df a, df b) {
     return df_zero();
 }
 
+// ---------------------------------------------------------------------------
+// dfloat: a double-float number used as an iterate type.  The mixed path's
+// polish phase runs the iteration kernels in dfloat instead of FP64: the
+// same 8 bytes per value, about 48 bits of significand, and only FP32
+// instructions, so the step kernels stay bound by memory rather than by the
+// FP64 pipe.  The exponent range is FP32's; values beyond it are infinite,
+// as in the FP32 path.  Device operators follow the df routines above.
+// ---------------------------------------------------------------------------
+struct dfloat {
+    float hi, lo;
+    dfloat() = default;
+    LPB_HD constexpr dfloat(int v) : hi((float)v), lo(0.0f) {}
+    LPB_HD constexpr dfloat(float h) : hi(h), lo(0.0f) {}
+    LPB_HD constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    // nearest pair to v; an infinite or overflowing v keeps lo = 0
+    LPB_HD explicit dfloat(double v) : hi((float)v), lo(0.0f) {
+        if (std::isfinite(hi)) lo = (float)(v - (double)hi);
+    }
+    LPB_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+static_assert(sizeof(dfloat) == sizeof(df) && alignof(dfloat) == alignof(df), "dfloat and df share a layout");
+
+LPB_HD df df_of(dfloat a) { return df{a.hi, a.lo}; }
+LPB_HD dfloat dfl_of(df a) { return dfloat(a.hi, a.lo); }
+
+LPB_HD dfloat operator+(dfloat a, dfloat b) { return dfl_of(df_add(df_of(a), df_of(b))); }
+LPB_HD dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+LPB_HD dfloat operator-(dfloat a, dfloat b) { return dfl_of(df_add(df_of(a), df{-b.hi, -b.lo})); }
+LPB_HD dfloat operator*(dfloat a, dfloat b) { return dfl_of(df_mul(df_of(a), df_of(b))); }
+// a / b: quotient of the leading parts, corrected once by the remainder
+LPB_HD dfloat operator/(dfloat a, dfloat b) {
+    const float q1 = a.hi / b.hi;
+    const df r = df_sub(df_of(a), df_mulf(df_of(b), q1));
+    const float q2 = r.hi / b.hi;
+    return dfl_of(quick_two_sum(q1, q2));
+}
+LPB_HD dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+LPB_HD bool operator<(dfloat a, dfloat b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+LPB_HD bool operator>(dfloat a, dfloat b) { return b < a; }
+LPB_HD bool operator==(dfloat a, dfloat b) { return a.hi == b.hi && a.lo == b.lo; }
+
+// acc + a * x with the product kept to df accuracy (the inner product step
+// of the dfloat SpMMs)
+LPB_HD dfloat dfl_fma(dfloat a, dfloat x, dfloat acc) {
+    const df p = two_prod(a.hi, x.hi);
+    const df s = two_sum(acc.hi, p.hi);
+    const float e = s.lo + acc.lo + fmaf(a.hi, x.lo, fmaf(a.lo, x.hi, p.lo));
+    return dfl_of(quick_two_sum(s.hi, e));
+}
+
+// acc += w * x for a df constant and a dfloat x (the check SpMMs)
+LPB_HD void df_fma_acc(df& acc, df w, dfloat x) {
+    const df p = two_prod(w.hi, x.hi);
+    const df s = two_sum(acc.hi, p.hi);
+    acc.hi = s.hi;
+    acc.lo += s.lo + fmaf(w.hi, x.lo, fmaf(w.lo, x.hi, p.lo));
+}
+
 }  // namespace lpb

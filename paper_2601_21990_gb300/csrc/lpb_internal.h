@@ -71,6 +71,7 @@ template <typename T>
 struct ColParams {
     int* kind;   // override kind
     int* var;    // override variable (or -1)
+    int* grp;    // restart group of the column (its Halpern weights)
     T* lo;       // kind 1: scaled box of var (intersected with the base box)
     T* hi;
     T* c;        // kind 2: scaled objective coefficient of var
@@ -86,7 +87,8 @@ struct ColCheck {
     double* hi;
     double* c;    // kind 2: sign
     double* w;    // primal weight
-    int* lp;      // LP index of the column in the caller's batch
+    int* grp;     // restart group of the column
+    int* slot;    // the LP's slot in its group's range of the residual scratch
     double* best; // smallest KKT error seen since the last halving (stall test)
     int* stall;   // checks since the KKT error last halved
 };
@@ -99,16 +101,26 @@ struct ColRecord {
     double obj, dual_obj, rel_primal, rel_dual, rel_gap;
 };
 
-// Batch state that lives on the device between checks.
+// State of one restart group on the device.  A group is the set of LPs
+// solved as one batch in the sense of Sec. 5: they share the batch-averaged
+// restart test and the Halpern index k.  A lane (the active columns of one
+// handle in one iterate precision) holds any number of groups side by side;
+// a plain batched solve is one group.
 struct Control {
-    int k;          // inner index of the first iteration of the next interval
-    int restart;    // 1 if the last check restarted
-    int error;      // device-side check flags (LPB_ERR_*)
-    int stalled;    // 1 if an active LP stalled at the last check
-    double r0;      // residual at the start of the epoch (< 0: unset)
-    double r_prev;  // residual at the previous check
-    double r_avg;   // averaged residual of the last check
+    int k;            // inner index of the group's next iteration
+    int restart;      // 1 if the last check restarted the group
+    int error;        // device-side admission flags (LPB_ERR_*)
+    int stalled;      // 1 if an active LP of the group stalled at the last check
+    double r0;        // residual at the start of the epoch (< 0: unset)
+    double r_prev;    // residual at the previous check
+    double r_avg;     // averaged residual of the last check
     int64_t restarts;
+    int64_t K;        // iterations the group has run
+    int64_t max_iter;
+    double tol, eps_inf;
+    int slot0, nslots;  // the group's LPs own residual slots [slot0, slot0 + nslots)
+    int active;
+    int pad;
 };
 
 // records the message lpb_last_error() returns on this thread (lpb_api.cu)
@@ -160,11 +172,13 @@ struct IterData {
 // One reflected-Halpern PDHG iteration on columns [0, ncol): primal step
 // (A~^T Y fused with the box projection, reflection and Halpern update) then
 // dual step (A~ Xbar fused with the row projection and Halpern update).
-// hal[2t], hal[2t+1] are the Halpern weights (k+1)/(k+2), 1/(k+2) of
-// Eq. mainiter for iteration t of the interval, written on the device.
+// hal[2 (g ce + t)], hal[2 (g ce + t) + 1] are the Halpern weights
+// (k+1)/(k+2), 1/(k+2) of Eq. mainiter for iteration t of the interval of
+// restart group g (ce = check_every), written on the device by the checks.
+// uni >= 0 says that every active column belongs to group uni.
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol,
-                             const T* hal, int t, bool check, cudaStream_t s,
+                             const T* hal, int t, int ce, int uni, bool check, cudaStream_t s,
                              cudaEvent_t* ev /* 3 events or nullptr */);
 
 // ---------------------------------------------------------------------------
@@ -176,38 +190,63 @@ struct CheckData {
     const double *d_r, *d_c;
     const double *c, *xl, *xu;     // original base vectors (n)
     const double *l, *u;           // original row bounds (m)
-    ColCheck col;
-    double eta, beta_s, beta_n, beta_a, theta, mnorm_sign, eps_inf, tol;
+    ColCheck col;                  // the lane's columns
+    double eta, beta_s, beta_n, beta_a, theta, mnorm_sign;
     int detect_inf, restart_to_output;
     int stall_checks;              // 0: no stall test
     int check_every;
-    double* hal64;                 // Halpern weights of the next interval (2 * check_every)
-    float* hal32;
+    // the lane's restart groups
+    Control* ctl;                  // gcap groups
+    int gcap;
+    double* hal64;                 // Halpern weights of each group's next interval,
+    float* hal32;                  //   [gcap][check_every][2], in each iterate type
+    dfloat* haldf;
+    double* rscr;                  // per-LP residual slots of the averaged restart test
+    int* rtag;
+    int* flags;                    // [0]: a group restarted at the last check
     // double-float copies for the FP32-iterate checks: scalings, their
     // reciprocals, original c, xlo, xhi (n) and l, u (m)
     const df *f_dr, *f_dc, *f_idr, *f_idc, *f_c, *f_xl, *f_xu, *f_l, *f_u;
 };
 
+// The checks of an interval of interval_len iterations on columns [0, ncol):
+// FP64-accurate KKT statistics, per-LP status, then each restart group's
+// averaged restart test and primal-weight update and the anchor copies.
 template <typename T>
-cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int64_t k_eval_global,
-                         int interval_len, bool final_check, double* P, double* Q, double* partials,
-                         double* colsum, ColRecord* rec, Control* ctl, ColParams<T> colp, cudaStream_t s,
-                         cudaEvent_t* ev /* 3 events or nullptr */);
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len, int tag,
+                         double* P, double* Q, double* partials, double* colsum, ColRecord* rec, ColParams<T> colp,
+                         cudaStream_t s, cudaEvent_t* ev /* 3 events or nullptr */);
 
+// Admits count LPs (specs_dev) into columns [c0, c0 + count) as restart
+// group `group` with residual slots [slot0, slot0 + count): per-column data,
+// the group's control record and Halpern table, and the starting iterates.
+// LP q starts from warm_x + q * wsx, warm_y + q * wsy (device, original
+// space; stride 0 gives every LP the same start), or from zero when null.
 template <typename T>
-cudaError_t launch_init(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int ncol,
-                        const lpb_lp_spec* specs_dev, const double* warm_x, const double* warm_y,
-                        double c_norm_base, double b_norm, ColRecord* rec, Control* ctl, cudaStream_t s);
+cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int c0, int count,
+                         int group, int slot0, const lpb_lp_spec* specs_dev, const double* warm_x,
+                         const double* warm_y, int64_t wsx, int64_t wsy, double c_norm_base, double b_norm,
+                         double tol, double eps_inf, int64_t max_iter, ColRecord* rec, cudaStream_t s);
 
+// x, y of the finished columns cols_dev[f] in the original space, written to
+// outp_dev[f] (n values) and outp_dev[count + f] (m values); null pointers skip.
 template <typename T>
 cudaError_t launch_extract(const CheckData& d, const IterBufs<T>& b, int ld, const int* cols_dev,
-                           const int* lps_dev, int count, const double* xl_base, const double* xu_base,
-                           double* x_out, double* y_out, cudaStream_t s);
+                           double* const* outp_dev, int count, const double* xl_base, const double* xu_base,
+                           cudaStream_t s);
 
-// FP64 polish: widens the FP32 state (X, X0, Y, Y0) of the active batch to
-// FP64 and fills the FP64 per-column parameters from the FP64 originals.
-cudaError_t launch_promote(const CheckData& d, const IterBufs<float>& src, const IterBufs<double>& dst,
-                           ColParams<double> colp64, int ld, int ncol, cudaStream_t s);
+// Moves columns sc_dev[p] of an FP32 lane to columns dc_dev[p] of a polish
+// lane in precision TD (double or dfloat): the iterates and anchors widened,
+// the per-column data copied, the TD parameters rebuilt from the FP64
+// originals; the columns join group group_dst with slots shifted by slot_shift.
+template <typename TD>
+cudaError_t launch_migrate(const CheckData& src, const IterBufs<float>& sb, int lds, const CheckData& dst,
+                           const IterBufs<TD>& db, int ldd, ColParams<TD> dcolp, const int* sc_dev, const int* dc_dev,
+                           int count, int group_dst, int slot_shift, cudaStream_t s);
+
+// After the host copied a group's control record into dst.ctl[group]: its
+// slots start at slot0 and its Halpern table is rewritten for its k.
+cudaError_t launch_group_moved(const CheckData& dst, int group, int slot0, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int* src_dev, const int* dst_dev,

@@ -24,7 +24,9 @@
 // The per-column parameters of the block's column tile are staged in shared
 // memory once per block.  No FP64 instruction runs in the FP32 kernels
 // (GB300 executes FP64 at a small fraction of its FP32 rate); the Halpern
-// weights come from a table written by the check kernels.
+// weights come from a table written by the check kernels.  The kernels are
+// instantiated for float (mixed path), double (FP64 path) and dfloat (the
+// mixed path's polish phase: double-float values on the FP32 pipe).
 #include "lpb_internal.h"
 
 // resident blocks per SM the step kernels are compiled for (register cap)
@@ -39,6 +41,7 @@ namespace {
 template <typename T> struct Vec;
 template <> struct Vec<float> { static constexpr int V = 4; };
 template <> struct Vec<double> { static constexpr int V = 2; };
+template <> struct Vec<dfloat> { static constexpr int V = 2; };
 
 __device__ __forceinline__ void ldv(const float* p, float (&r)[4]) {
     float4 u = *reinterpret_cast<const float4*>(p);
@@ -62,6 +65,39 @@ __device__ __forceinline__ void stv(float* p, const float (&r)[4]) {
 __device__ __forceinline__ void stv(double* p, const double (&r)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
 }
+__device__ __forceinline__ void ldv(const dfloat* p, dfloat (&r)[2]) {
+    float4 u = *reinterpret_cast<const float4*>(p);
+    r[0] = dfloat(u.x, u.y); r[1] = dfloat(u.z, u.w);
+}
+__device__ __forceinline__ void ldg_v(const dfloat* p, dfloat (&r)[2]) {
+    float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = dfloat(u.x, u.y); r[1] = dfloat(u.z, u.w);
+}
+__device__ __forceinline__ void stv(dfloat* p, const dfloat (&r)[2]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0].hi, r[0].lo, r[1].hi, r[1].lo);
+}
+
+// scalar read-only load, shuffle, multiply-add and infinity test for each
+// iterate type
+__device__ __forceinline__ float ldg1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldg1(const double* p) { return __ldg(p); }
+__device__ __forceinline__ dfloat ldg1(const dfloat* p) {
+    const float2 u = __ldg(reinterpret_cast<const float2*>(p));
+    return dfloat(u.x, u.y);
+}
+template <typename T>
+__device__ __forceinline__ T shfl(unsigned mask, T v, int src, int width) {
+    return __shfl_sync(mask, v, src, width);
+}
+__device__ __forceinline__ dfloat shfl(unsigned mask, dfloat v, int src, int width) {
+    return dfloat(__shfl_sync(mask, v.hi, src, width), __shfl_sync(mask, v.lo, src, width));
+}
+__device__ __forceinline__ float mad(float a, float x, float acc) { return fmaf(a, x, acc); }
+__device__ __forceinline__ double mad(double a, double x, double acc) { return fma(a, x, acc); }
+__device__ __forceinline__ dfloat mad(dfloat a, dfloat x, dfloat acc) { return dfl_fma(a, x, acc); }
+__device__ __forceinline__ bool is_inf(float v) { return isinf(v); }
+__device__ __forceinline__ bool is_inf(double v) { return isinf(v); }
+__device__ __forceinline__ bool is_inf(dfloat v) { return isinf(v.hi); }
 
 // One round of a row's entries: the G lanes of the row group load up to
 // R = G*K of the row's (col, value) pairs at once (K per lane, coalesced);
@@ -81,7 +117,7 @@ __device__ __forceinline__ void load_round(const int* __restrict__ ci, const T* 
     for (int q = 0; q < K; ++q) {
         const int me = e0 + q * G + lane;
         c[q] = me < end ? __ldg(ci + me) : 0;
-        a[q] = me < end ? __ldg(va + me) : T(0);
+        a[q] = me < end ? ldg1(va + me) : T(0);
     }
 }
 
@@ -106,7 +142,7 @@ __device__ __forceinline__ void gather_round(const int (&c)[Round<T, G>::K], con
         for (int j = 0; j < 4; ++j) {
             const int k = k0 + j;
             const int cs = __shfl_sync(gmask, c[k / G], k % G, G);
-            const T as = __shfl_sync(gmask, a[k / G], k % G, G);
+            const T as = shfl(gmask, a[k / G], k % G, G);
             cc[j] = k < cnt ? cs : cfirst;
             aa[j] = k < cnt ? as : T(0);
         }
@@ -117,10 +153,10 @@ __device__ __forceinline__ void gather_round(const int (&c)[Round<T, G>::K], con
         ldg_v(src + (size_t)cc[3] * ld + colg, x3);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            acc[v] = fma(aa[0], x0[v], acc[v]);
-            acc[v] = fma(aa[1], x1[v], acc[v]);
-            acc[v] = fma(aa[2], x2[v], acc[v]);
-            acc[v] = fma(aa[3], x3[v], acc[v]);
+            acc[v] = mad(aa[0], x0[v], acc[v]);
+            acc[v] = mad(aa[1], x1[v], acc[v]);
+            acc[v] = mad(aa[2], x2[v], acc[v]);
+            acc[v] = mad(aa[3], x3[v], acc[v]);
         }
     }
 }
@@ -161,8 +197,9 @@ struct StepArgs {
     const T* rhi;
     ColParams<T> col;
     int ld, ncol;
-    const T* hal;     // (k+1)/(k+2), 1/(k+2) of Eq. mainiter for each t of the interval
-    int t;
+    const T* hal;     // per group g: (k+1)/(k+2), 1/(k+2) of Eq. mainiter at [2 (g ce + t)]
+    int t, ce;
+    int uni;          // the group of every active column, or -1 if they belong to several
 };
 
 // Reduce the row groups' partial sums of a long row through shared memory;
@@ -183,17 +220,18 @@ __device__ __forceinline__ bool long_row_reduce(T (&acc)[V], T* red) {
 
 template <typename T>
 __device__ __forceinline__ T barrier(T v, T lo, T hi) {
-    const bool li = isinf(lo), hi_ = isinf(hi);
+    const bool li = is_inf(lo), hi_ = is_inf(hi);
     if (li && hi_) return T(0);
     if (li) return v > T(0) ? v : T(0);
     if (hi_) return v < T(0) ? v : T(0);
     return v;
 }
 
-// per-column parameters of the block's column tile, staged in shared memory
+// per-column parameters of the block's column tile, staged in shared memory;
+// ca, cb are the Halpern weights of the column's restart group
 template <typename T, int TN>
 struct TileParams {
-    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN];
+    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN], ca[TN], cb[TN];
     int kind[TN], var[TN];
 };
 
@@ -201,13 +239,12 @@ struct TileParams {
 // offset in the tile): box projection, reflection, Halpern update
 template <typename T, int V, int TN, bool CHECK>
 __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const TileParams<T, TN>& P, int row, int col0,
-                                                int q0, const T (&acc)[V]) {
+                                                int q0, const T (&acc)[V], T uca, T ucb) {
     const size_t off = (size_t)row * a.ld + col0;
     T x[V], x0[V];
     ldv(a.Z + off, x);
     ldv(a.Z0 + off, x0);
     const T cr = a.rc[row], lor = a.rlo[row], hir = a.rhi[row];
-    const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
     T xh[V], xb[V], xn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -223,6 +260,7 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
         s = s > lo ? s : lo;
         xh[v] = s;
         xb[v] = T(2) * s - x[v];
+        const T ca = a.uni >= 0 ? uca : P.ca[q], cb = a.uni >= 0 ? ucb : P.cb[q];
         xn[v] = ca * xb[v] + cb * x0[v];
         // x^ - x: where the box is not active it is -tau (c + G) exactly,
         // which stays accurate when |x| is large (diverging iterates of an
@@ -240,13 +278,12 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
 // dual epilogue: row projection and Halpern update
 template <typename T, int V, int TN, bool CHECK>
 __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TileParams<T, TN>& P, int row, int col0,
-                                              int q0, const T (&acc)[V]) {
+                                              int q0, const T (&acc)[V], T uca, T ucb) {
     const size_t off = (size_t)row * a.ld + col0;
     T y[V], y0[V];
     ldv(a.Z + off, y);
     ldv(a.Z0 + off, y0);
     const T lr = a.rlo[row], ur = a.rhi[row];
-    const T ca = a.hal[2 * a.t], cb = a.hal[2 * a.t + 1];
     T yh[V], yn[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -255,6 +292,7 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
         T p = s < ur ? s : ur;
         p = p > lr ? p : lr;
         yh[v] = sg * (s - p);
+        const T ca = a.uni >= 0 ? uca : P.ca[q0 + v], cb = a.uni >= 0 ? ucb : P.cb[q0 + v];
         yn[v] = ca * (T(2) * yh[v] - y[v]) + cb * y0[v];
         // y^ - y: y^ = 0 exactly where the row bound is not active; where it
         // is, y^ - y = sigma (A xb - Pi(v)) without the cancellation of y
@@ -287,7 +325,12 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
     const int tile0 = blockIdx.y * TN;
     for (int q = threadIdx.x; q < TN; q += kBlock) {
         const int j = tile0 + q;
-        const bool in = j < a.ld;
+        const bool in = j < a.ncol;
+        if (a.uni < 0) {
+            const int h = in ? 2 * (a.col.grp[j] * a.ce + a.t) : 0;
+            P.ca[q] = in ? a.hal[h] : T(0);
+            P.cb[q] = in ? a.hal[h + 1] : T(0);
+        }
         if (PRIMAL) {
             P.kind[q] = in ? a.col.kind[j] : 0;
             P.var[q] = in ? a.col.var[j] : -1;
@@ -300,6 +343,9 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
         }
     }
     __syncthreads();
+    // one restart group in the whole batch: its Halpern weights as scalars
+    const int hu = a.uni >= 0 ? 2 * (a.uni * a.ce + a.t) : 0;
+    const T uca = a.uni >= 0 ? a.hal[hu] : T(0), ucb = a.uni >= 0 ? a.hal[hu + 1] : T(0);
     const int col0 = tile0 + lane * V;
     const bool active = col0 < a.ncol;
     const int colg = active ? col0 : tile0;
@@ -315,8 +361,8 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
         for (int v = 0; v < V; ++v) acc[v] = T(0);
         gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg, end, gmask, acc);
         if (!long_row_reduce<T, V, G>(acc, red) || !active) return;
-        if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc);
-        else dual_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc);
+        if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc, uca, ucb);
+        else dual_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc, uca, ucb);
         return;
     }
 
@@ -350,8 +396,8 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
         // the next row's first index round, issued before this row's epilogue
         if (rn < a.rows) load_round<T, G>(a.ci, a.va, nbeg, nend - nbeg <= kLongRow ? nend : nbeg, c, av);
         if (is_short && active) {
-            if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc);
-            else dual_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc);
+            if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc, uca, ucb);
+            else dual_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc, uca, ucb);
         }
         r = rn;
         beg = nbeg;
@@ -403,7 +449,7 @@ cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, cudaStr
 
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol, const T* hal, int t,
-                             bool check, cudaStream_t s, cudaEvent_t* ev) {
+                             int ce, int uni, bool check, cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
     StepArgs<T> p{};
     p.rows = d.At.rows;
@@ -427,6 +473,8 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.ncol = ncol;
     p.hal = hal;
     p.t = t;
+    p.ce = ce;
+    p.uni = uni;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     if ((e = dispatch_step<T>(true, check, p, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
@@ -453,14 +501,18 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.ncol = ncol;
     q.hal = hal;
     q.t = t;
+    q.ce = ce;
+    q.uni = uni;
     if ((e = dispatch_step<T>(false, check, q, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 template cudaError_t launch_iteration<float>(const IterData<float>&, const IterBufs<float>&, int, int, const float*,
-                                             int, bool, cudaStream_t, cudaEvent_t*);
+                                             int, int, int, bool, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_iteration<double>(const IterData<double>&, const IterBufs<double>&, int, int,
-                                              const double*, int, bool, cudaStream_t, cudaEvent_t*);
+                                              const double*, int, int, int, bool, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_iteration<dfloat>(const IterData<dfloat>&, const IterBufs<dfloat>&, int, int,
+                                              const dfloat*, int, int, int, bool, cudaStream_t, cudaEvent_t*);
 
 }  // namespace lpb

@@ -25,11 +25,17 @@ ERR_NAMES = ["LPB_OK", "LPB_ERR_INVALID_ARG", "LPB_ERR_OOM", "LPB_ERR_CUDA", "LP
 OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITERATION_LIMIT, NUMERICAL = range(5)
 STATUS_NAMES = ["OPTIMAL", "PRIMAL_INFEASIBLE", "DUAL_INFEASIBLE", "ITERATION_LIMIT", "NUMERICAL"]
 FP64, MIXED = 0, 1
+POLISH_DFLOAT, POLISH_FP64 = 0, 1
 
 # every symbol include/lpb.h declares
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
            "lpb_result_device", "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_batch_free",
            "lpb_destroy", "lpb_last_error", "lpb_scaling_noalloc"]
+# every symbol include/lpb_serve.h declares
+SERVE_EXPORTS = ["lpb_server_default_options", "lpb_server_create", "lpb_server_attach", "lpb_server_submit",
+                 "lpb_server_poll", "lpb_server_wait", "lpb_server_result", "lpb_server_results",
+                 "lpb_server_request_info", "lpb_server_release", "lpb_server_stats_get", "lpb_server_destroy"]
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
 
 class LpbError(RuntimeError):
@@ -45,7 +51,8 @@ class Options(C.Structure):
                 ("restart_to_pdhg_output", C.c_int32), ("power_max_iter", C.c_int32),
                 ("power_tol", C.c_double), ("power_seed", C.c_uint64), ("eps_infeas", C.c_double),
                 ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32)]
+                ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32),
+                ("polish_arith", C.c_int32)]
 
 
 class Spec(C.Structure):
@@ -63,6 +70,31 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("bytes", C.c_double * 4),
                 ("setup_ms", C.c_double), ("checks", C.c_int64), ("compactions", C.c_int64),
                 ("kernels", C.c_int64), ("fp64_switch_iter", C.c_int64)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("lane_columns", C.c_int32), ("polish_columns", C.c_int32),
+                ("max_groups", C.c_int32), ("device", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("matrix_id", C.c_int32), ("num_lps", C.c_int32), ("specs", C.c_void_p), ("tol", C.c_double),
+                ("max_iter", C.c_int64), ("warm_x", C.c_void_p), ("warm_y", C.c_void_p),
+                ("warm_request", C.c_int64), ("warm_lp", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("num_lps", C.c_int32), ("optimal", C.c_int32), ("infeasible", C.c_int32),
+                ("iteration_limit", C.c_int32), ("other", C.c_int32), ("iters", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("footprint_bytes", C.c_int64), ("polished", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("done", C.c_int64), ("lps_solved", C.c_int64), ("intervals", C.c_int64),
+                ("column_iters", C.c_int64), ("admitted_while_busy", C.c_int64), ("migrations", C.c_int64),
+                ("busy_s", C.c_double), ("hbm_used_bytes", C.c_int64), ("hbm_budget_bytes", C.c_int64),
+                ("kernels", C.c_int64)]
 
 
 SPEC_DTYPE = np.dtype([("kind", "<i4"), ("var", "<i4"), ("lo", "<f8"), ("hi", "<f8"), ("sign", "<f8")])
@@ -97,8 +129,24 @@ def load(path: str = LIB_PATH):
     lib.lpb_destroy.restype = None
     lib.lpb_last_error.restype = C.c_char_p
     lib.lpb_scaling_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.lpb_server_default_options.argtypes = [C.POINTER(ServerOptions)]
+    lib.lpb_server_default_options.restype = None
+    lib.lpb_server_create.argtypes = [C.POINTER(ServerOptions), C.POINTER(vp)]
+    lib.lpb_server_attach.argtypes = [vp, vp, C.POINTER(i32)]
+    lib.lpb_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(i64)]
+    lib.lpb_server_poll.argtypes = [vp, i64, C.POINTER(i32)]
+    lib.lpb_server_wait.argtypes = [vp, i64, d]
+    lib.lpb_server_result.argtypes = [vp, i64, i32, C.POINTER(Result), vp, vp]
+    lib.lpb_server_results.argtypes = [vp, i64, vp]
+    lib.lpb_server_request_info.argtypes = [vp, i64, C.POINTER(RequestInfo)]
+    lib.lpb_server_release.argtypes = [vp, i64]
+    lib.lpb_server_stats_get.argtypes = [vp, C.POINTER(ServerStats)]
+    lib.lpb_server_destroy.argtypes = [vp]
+    lib.lpb_server_destroy.restype = None
     for f in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results", "lpb_result_device",
-              "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_scaling_noalloc"):
+              "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_scaling_noalloc", "lpb_server_create",
+              "lpb_server_attach", "lpb_server_submit", "lpb_server_poll", "lpb_server_wait", "lpb_server_result",
+              "lpb_server_results", "lpb_server_request_info", "lpb_server_release", "lpb_server_stats_get"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -219,6 +267,86 @@ def lpb_last_error() -> str:
     return load().lpb_last_error().decode()
 
 
+# include/lpb_serve.h
+
+def lpb_server_default_options(**overrides) -> ServerOptions:
+    o = ServerOptions()
+    load().lpb_server_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def lpb_server_create(options: ServerOptions | None = None):
+    s = C.c_void_p()
+    _check(load().lpb_server_create(C.byref(options) if options is not None else None, C.byref(s)))
+    return s
+
+
+def lpb_server_attach(srv, h) -> int:
+    mid = C.c_int32()
+    _check(load().lpb_server_attach(srv, h, C.byref(mid)))
+    return mid.value
+
+
+def lpb_server_submit(srv, matrix_id: int, specs: np.ndarray, tol: float, max_iter: int, warm_x=None, warm_y=None,
+                      warm_request: int = -1, warm_lp: int = 0) -> int:
+    sp = np.ascontiguousarray(specs, dtype=SPEC_DTYPE)
+    wx = None if warm_x is None else np.ascontiguousarray(warm_x, dtype=np.float64)
+    wy = None if warm_y is None else np.ascontiguousarray(warm_y, dtype=np.float64)
+    q = Request(int(matrix_id), int(sp.shape[0]), _ptr(sp), float(tol), int(max_iter), _ptr(wx), _ptr(wy),
+                int(warm_request), int(warm_lp))
+    rid = C.c_int64()
+    _check(load().lpb_server_submit(srv, C.byref(q), C.byref(rid)))
+    return rid.value
+
+
+def lpb_server_poll(srv, rid: int) -> bool:
+    done = C.c_int32()
+    _check(load().lpb_server_poll(srv, int(rid), C.byref(done)))
+    return bool(done.value)
+
+
+def lpb_server_wait(srv, rid: int, timeout_s: float = -1.0) -> None:
+    _check(load().lpb_server_wait(srv, int(rid), float(timeout_s)))
+
+
+def lpb_server_result(srv, rid: int, lp: int, n: int, m: int, want_xy: bool = True):
+    r = Result()
+    x = np.zeros(n) if want_xy else None
+    y = np.zeros(max(m, 1)) if want_xy else None
+    _check(load().lpb_server_result(srv, int(rid), int(lp), C.byref(r), _ptr(x), _ptr(y)))
+    return r, x, (y[:m] if y is not None else None)
+
+
+def lpb_server_results(srv, rid: int, num_lps: int) -> np.ndarray:
+    out = (Result * max(num_lps, 1))()
+    _check(load().lpb_server_results(srv, int(rid), out))
+    return np.ctypeslib.as_array(out)[:num_lps].copy()
+
+
+def lpb_server_request_info(srv, rid: int) -> RequestInfo:
+    info = RequestInfo()
+    _check(load().lpb_server_request_info(srv, int(rid), C.byref(info)))
+    return info
+
+
+def lpb_server_release(srv, rid: int) -> None:
+    _check(load().lpb_server_release(srv, int(rid)))
+
+
+def lpb_server_stats_get(srv) -> ServerStats:
+    st = ServerStats()
+    _check(load().lpb_server_stats_get(srv, C.byref(st)))
+    return st
+
+
+def lpb_server_destroy(srv) -> None:
+    load().lpb_server_destroy(srv)
+
+
 # ---------------------------------------------------------------------------
 # conveniences
 # ---------------------------------------------------------------------------
@@ -310,6 +438,59 @@ class Handle:
     def close(self):
         if self.ptr is not None:
             lpb_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of solve requests over attached handles."""
+
+    def __init__(self, options: ServerOptions | None = None, **opts):
+        if options is None:
+            options = lpb_server_default_options(**opts)
+        self.ptr = lpb_server_create(options)
+        self.handles = []
+
+    def attach(self, handle: Handle) -> int:
+        mid = lpb_server_attach(self.ptr, handle.ptr)
+        self.handles.append(handle)
+        return mid
+
+    def submit(self, matrix_id: int, specs, tol: float = 1e-4, max_iter: int = 100000, warm_x=None, warm_y=None,
+               warm_request: int = -1, warm_lp: int = 0) -> int:
+        sp = specs if isinstance(specs, np.ndarray) else specs_from(specs)
+        return lpb_server_submit(self.ptr, matrix_id, sp, tol, max_iter, warm_x, warm_y, warm_request, warm_lp)
+
+    def poll(self, rid: int) -> bool:
+        return lpb_server_poll(self.ptr, rid)
+
+    def wait(self, rid: int, timeout_s: float = -1.0) -> None:
+        lpb_server_wait(self.ptr, rid, timeout_s)
+
+    def info(self, rid: int) -> RequestInfo:
+        return lpb_server_request_info(self.ptr, rid)
+
+    def results(self, rid: int) -> np.ndarray:
+        return lpb_server_results(self.ptr, rid, self.info(rid).num_lps)
+
+    def result(self, rid: int, matrix_id: int, lp: int, want_xy: bool = True):
+        h = self.handles[matrix_id]
+        return lpb_server_result(self.ptr, rid, lp, h.n, h.m, want_xy)
+
+    def release(self, rid: int) -> None:
+        lpb_server_release(self.ptr, rid)
+
+    def stats(self) -> ServerStats:
+        return lpb_server_stats_get(self.ptr)
+
+    def close(self):
+        if self.ptr is not None:
+            lpb_server_destroy(self.ptr)
             self.ptr = None
 
     def __del__(self):

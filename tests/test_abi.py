@@ -10,6 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lpb.h")
+SERVE_HEADER = os.path.join(ROOT, "include", "lpb_serve.h")
 
 
 @pytest.fixture(scope="module")
@@ -20,8 +21,8 @@ def lib():
     return lpb.load()
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:lpb_err|void|const char\*)\s+(lpb_\w+)\s*\(", text, flags=re.M)))
 
@@ -34,7 +35,7 @@ def test_header_declares_the_expected_calls():
 
 
 def test_library_exports_every_declared_symbol(lib):
-    for name in declared_functions():
+    for name in declared_functions() + declared_functions(SERVE_HEADER):
         assert hasattr(lib, name), name
 
 
@@ -42,6 +43,43 @@ def test_binding_lists_every_declared_symbol():
     from paper_2601_21990_gb300 import lpb
 
     assert sorted(lpb.EXPORTS) == declared_functions()
+    assert sorted(lpb.SERVE_EXPORTS) == declared_functions(SERVE_HEADER)
+
+
+def test_serve_struct_layouts_match_header(tmp_path):
+    from paper_2601_21990_gb300 import lpb
+
+    src = tmp_path / "szs.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "lpb_serve.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(lpb_server_options), sizeof(lpb_request), sizeof(lpb_request_info),
+         sizeof(lpb_server_stats));
+  printf("%zu %zu %zu\\n", offsetof(lpb_request, warm_request), offsetof(lpb_request_info, t_submit),
+         offsetof(lpb_server_stats, busy_s));
+  return 0;
+}
+""")
+    exe = tmp_path / "szs"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    v = [int(x) for x in subprocess.check_output([str(exe)]).decode().split()]
+    assert v[:4] == [ctypes.sizeof(lpb.ServerOptions), ctypes.sizeof(lpb.Request), ctypes.sizeof(lpb.RequestInfo),
+                     ctypes.sizeof(lpb.ServerStats)]
+    assert v[4:] == [lpb.Request.warm_request.offset, lpb.RequestInfo.t_submit.offset, lpb.ServerStats.busy_s.offset]
+
+
+def test_server_create_without_device_fails_cleanly(lib):
+    """No GPU here: creating a server returns an error code, never aborts."""
+    import torch
+
+    from paper_2601_21990_gb300 import lpb
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lpb.LpbError):
+        lpb.Server()
 
 
 def test_default_options(lib):

@@ -451,12 +451,15 @@ def test_device_path_matches_host_path(lpb):
     assert xd and yd
 
 
-def test_fp64_polish_switch(lpb, orc):
-    """Forcing the FP32 -> FP64 switch early (stall after one check without
-    halving) still gives the oracle's results, and the switch is reported."""
+@pytest.mark.parametrize("arith", ["dfloat", "fp64"])
+def test_polish_switch(lpb, orc, arith):
+    """Forcing the FP32 -> polish switch early (stall after one check without
+    halving) still gives the oracle's results, with double-float and with
+    native FP64 polish iterates, and the switch is reported."""
     w = lpgen.sb_small(seed=3)
     ref = oracle_ref(orc, w.lp, w.specs)
-    h = lpb.Handle(w.lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1)
+    code = lpb.POLISH_DFLOAT if arith == "dfloat" else lpb.POLISH_FP64
+    h = lpb.Handle(w.lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1, polish_arith=code)
     b = h.solve(w.specs, tol=1e-6, max_iter=200000)
     assert b.profile().fp64_switch_iter >= 64
     assert_parity(orc, w.lp, w.specs, b, ref)
@@ -464,3 +467,29 @@ def test_fp64_polish_switch(lpb, orc):
     h2 = lpb.Handle(w.lp, precision=lpb.MIXED, fp64_polish=0)
     b2 = h2.solve(w.specs, tol=1e-4, max_iter=200000)
     assert b2.profile().fp64_switch_iter == -1
+
+
+@pytest.mark.parametrize("arith", ["dfloat", "fp64"])
+def test_obbt_polish_tight_tolerance(lpb, orc, arith):
+    """At rel-KKT 1e-6 the FP32 iterates of the 10k OBBT batch stall and the
+    polish phase takes the LPs to the tolerance: at least 90% end optimal
+    within the iteration cap, every optimal LP's objective matches the
+    oracle's to 1e-5, and sampled optimal LPs meet 1e-6 in the oracle's own
+    KKT evaluation."""
+    w = lpgen.obbt_square(seed=0, m=10000, n=10000, lps=64)
+    ref = golden_ref("obbt_square_10k_seed0")
+    code = lpb.POLISH_DFLOAT if arith == "dfloat" else lpb.POLISH_FP64
+    h = lpb.Handle(w.lp, precision=lpb.MIXED, polish_arith=code)
+    b = h.solve(w.specs, tol=1e-6, max_iter=200000)
+    assert b.profile().fp64_switch_iter > 0
+    res = b.results()
+    st = res["status"]
+    assert np.mean(st == 0) >= 0.9, np.bincount(st)
+    assert np.all((st == 0) | (st == 3) | (st == ref.status)), (st, ref.status)
+    opt = np.nonzero((ref.status == 0) & (st == 0))[0]
+    err = np.abs(res["obj"][opt] - ref.obj[opt]) / (1.0 + np.abs(ref.obj[opt]))
+    assert err.max() <= 1e-5, (err.max(), opt[np.argmax(err)])
+    for q in [q for q in (0, 1, 31, 32, 33, 63) if st[q] == 0]:
+        r, x, y = b.result(q)
+        k = orc.kkt_spec(w.lp, w.specs, q, x, y)
+        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-6, (q, k)
