@@ -321,6 +321,31 @@ def run_serving(args, rank, world, local):
     srv.close()
 
 
+def cusparse_spmm(lp, ncol, dev, reps=20):
+    """The paper's SpMM engine on the dual step's shape: cuSPARSE CSR SpMM
+    (torch.sparse.mm) of A (FP32 values) by a dense n x ncol FP32 block, no
+    epilogue; microseconds per product and algorithmic GB/s (A's values and
+    indices, the dense block read once, the m x ncol product written)."""
+    import torch
+
+    a = torch.sparse_csr_tensor(torch.tensor(lp.row_ptr, dtype=torch.int32), torch.tensor(lp.col_idx),
+                                torch.tensor(lp.vals, dtype=torch.float32), size=(lp.m, lp.n)).to(dev)
+    x = torch.randn(lp.n, ncol, device=dev)
+    for _ in range(3):
+        y = torch.sparse.mm(a, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = torch.sparse.mm(a, x)
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    by = 8.0 * lp.nnz + 4.0 * (lp.m + 1) + 4.0 * ncol * (lp.n + lp.m)
+    del y
+    return {"us": us, "GBps": by / (us * 1e-6) / 1e9, "what": f"torch.sparse.mm (cuSPARSE) A @ X, X {lp.n}x{ncol} FP32"}
+
+
 def solved_count(res) -> int:
     st = res["status"]
     return int(np.sum((st == 0) | (st == 1) | (st == 2)))
@@ -372,7 +397,8 @@ def main():
     w = WORKLOADS[args.workload]["fn"](args.seed + rank)
     max_iter = WORKLOADS[args.workload]["max_iter"]
     precision = lpb.FP64 if w.precision == "fp64" else lpb.MIXED
-    opts = lpb.lpb_default_options(precision=precision, profile=1, device=local, cuda_stream=stream.cuda_stream)
+    # timed solves: CUDA graphs and programmatic dependent launch, no per-launch events
+    opts = lpb.lpb_default_options(precision=precision, profile=0, device=local, cuda_stream=stream.cuda_stream)
     h = lpb.Handle(w.lp, options=opts)
     specs_np = lpb.specs_from(w.specs)
     specs_dev = torch.from_numpy(specs_np.view(np.uint8).copy()).to(dev)
@@ -409,6 +435,19 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    gpu_launches = int(sum(p.kernels for p in profs))
+    # per-launch kernel times: the same solves again with CUDA events around
+    # every launch (plain launches; graphs and PDL need no events between kernels)
+    hp = lpb.Handle(w.lp, options=lpb.lpb_default_options(precision=precision, profile=1, device=local,
+                                                         cuda_stream=stream.cuda_stream))
+    prof_steps = max(1, min(args.steps, 3))
+    profs = []
+    for _ in range(prof_steps):
+        flush.zero_()
+        b = hp.solve_dev(specs_dev, tol=TOL, max_iter=max_iter)
+        profs.append(b.profile())
+        b.free()
+    hp.close()
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -429,7 +468,18 @@ def main():
     achieved = by[dom] / (ms[dom] / 1e3) / 1e9
     peak, peak_kind = measured_peak()
     traffic = ncu_traffic(["k_primal", "k_dual"][dom], args.workload)
-    gpu_launches = int(sum(p.kernels for p in profs))
+
+    # the paper's engine on the same shape, and the step time against the batch
+    # width (the synthetic analogue of the paper's SpMM-vs-N figure)
+    try:
+        cus = cusparse_spmm(w.lp, q, dev)
+    except Exception as ex:  # torch without CSR SpMM support on this device
+        cus = {"unavailable": str(ex)[:120]}
+    widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+    us_w, best_w = h.tune_batch(widths)
+    width_sweep = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
+                   "best_width": widths[best_w],
+                   "what": "one iteration (primal + dual step) on N copies of the base LP, plain launches"}
 
     # B=1 loop: the same kernels, one LP per solve
     b1_n = min(args.b1_lps, q)
@@ -483,9 +533,14 @@ def main():
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": traffic, "launches": int(la[dom]),
                          "avg_launch_us": 1e3 * ms[dom] / max(la[dom], 1),
+                         "timing": f"CUDA events around every launch over {prof_steps} profiled repeats of the "
+                                   "timed solve (plain launches)",
                          "other_kernel_GBps": by[1 - dom] / (ms[1 - dom] / 1e3) / 1e9 if ms[1 - dom] > 0 else None},
-            "time_split_ms_per_step": {"primal_step": ms[0] / args.steps, "dual_step": ms[1] / args.steps,
-                                       "check_spmm": ms[2] / args.steps, "check_reduce": ms[3] / args.steps},
+            "time_split_ms_per_step": {"primal_step": ms[0] / prof_steps, "dual_step": ms[1] / prof_steps,
+                                       "check_spmm": ms[2] / prof_steps, "check_reduce": ms[3] / prof_steps,
+                                       "what": "profiled repeats (plain launches, events around each)"},
+            "cusparse_dual_spmm": cus,
+            "width_sweep": width_sweep,
             "b1_loop": {"value": b1_value, "unit": UNIT, "lps": b1_n,
                         "batched_over_b1": value / world / b1_value if b1_value else None},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

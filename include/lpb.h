@@ -82,6 +82,16 @@ typedef struct {
     int32_t polish_arith;           /* arithmetic of the polish iterates: LPB_POLISH_DFLOAT (default;
                                        double-float pairs on the FP32 pipe, 8 bytes per value) or
                                        LPB_POLISH_FP64 (native FP64) */
+    double eps_dual;                /* tolerance of the relative dual residual alone; < 0 (default)
+                                       uses the solve's tol.  Bound tightening (Sec. 6 OBBT) uses 1e-8
+                                       so that the dual bound is safe */
+    int32_t use_graphs;             /* 1 (default): each interval (check_every iterations and the check)
+                                       is a CUDA graph, captured once per batch shape and replayed;
+                                       not used when profile = 1 */
+    int32_t use_pdl;                /* 1 (default): the step kernels of an interval are launched as
+                                       programmatic dependents, so each one's launch and parameter
+                                       staging overlap the end of the previous one; not used when
+                                       profile = 1 */
 } lpb_options;
 
 /* Values of lpb_options.polish_arith. */
@@ -106,6 +116,8 @@ typedef struct {
     double rel_primal;   /* ||Ax - Pi_[l,u](Ax)|| / (1 + ||Ax||) */
     double rel_dual;     /* ||c + A^T y + r|| / (1 + ||c||) */
     double rel_gap;      /* |c^T x + phi + phi| / (1 + |c^T x| + |phi + phi|) */
+    double safe_bound;   /* dual_obj - tol (1 + |c^T x| + |phi + phi|): the paper's OBBT bound on the
+                            optimal objective, shifted by its Delta (Sec. 6 "OBBT results") */
 } lpb_lp_result;
 
 /* Per-kernel timing gathered when lpb_options.profile = 1 (CUDA events on the
@@ -195,6 +207,48 @@ lpb_err lpb_scaling(lpb_handle h, double* d_row, double* d_col);
 lpb_err lpb_scaling_noalloc(int32_t m, int32_t n, int32_t nnz, const int32_t* row_ptr_dev,
                             const int32_t* col_idx_dev, const double* vals_dev, int32_t ruiz_iters,
                             int32_t pock_chambolle, double* d_row_dev, double* d_col_dev, void* cuda_stream);
+
+/* Bound tightening from a solved OBBT batch (Sec. 5.2, Sec. 6 "OBBT
+ * results").  For each LP q of kind 2 that ended LPB_OPTIMAL: sign +1
+ * (min x_var) gives the lower bound safe_bound, sign -1 (max x_var) the
+ * upper bound -safe_bound.  new_lo / new_hi (n doubles, host) start as
+ * var_lo / var_hi (n, host; the base box) and take a candidate only where it
+ * improves the current value by more than min_gain (the paper uses 1e-4)
+ * and stays inside the box; *updated counts the bounds changed.  specs are
+ * the batch's num_lps host records. */
+lpb_err lpb_obbt_tighten(lpb_batch_t b, const lpb_lp_spec* specs, const double* var_lo, const double* var_hi,
+                         double min_gain, double* new_lo, double* new_hi, int32_t* updated);
+
+/* Launch shapes of the two step kernels (Sec. 5 batched SpMMs).  A row of
+ * A~^T (primal step) or A~ (dual step) with more nonzeros than the
+ * long_row_* threshold is reduced by a whole thread block; shorter rows by a
+ * row group of lanes, whose number follows from the batch width and is
+ * halved lane_shift_* times (more column tiles per row).  Defaults: 32, 32,
+ * 0, 0.  Results depend on the shapes only through the order in which long
+ * rows are summed. */
+typedef struct {
+    int32_t long_row_primal;
+    int32_t long_row_dual;
+    int32_t lane_shift_primal;
+    int32_t lane_shift_dual;
+} lpb_tuning;
+
+lpb_err lpb_get_tuning(lpb_handle h, lpb_tuning* t);
+/* thresholds >= 1, shifts in [0, 5]; LPB_ERR_INVALID_ARG otherwise */
+lpb_err lpb_set_tuning(lpb_handle h, const lpb_tuning* t);
+
+/* Autotuner: times the primal and dual steps on num_lps copies of the base
+ * LP for every threshold in {8, 16, 32, 64, 128, 256} and shift in {0, 1, 2},
+ * applies the fastest shape of each step to the handle and returns it in
+ * *chosen (may be NULL).  Takes a few hundred step launches. */
+lpb_err lpb_autotune(lpb_handle h, int32_t num_lps, lpb_tuning* chosen);
+
+/* Batch size by timing (Sec. 5: pick the N that maximises mat-vec products
+ * per second): for each of count batch widths, the time of one iteration
+ * (primal + dual step) on that many copies of the base LP, in microseconds,
+ * into us_per_iter[i]; *best = the index with the most LP iterations per
+ * second.  Widths must be in [1, 65536]. */
+lpb_err lpb_tune_batch(lpb_handle h, const int32_t* widths, int32_t count, double* us_per_iter, int32_t* best);
 
 void lpb_batch_free(lpb_batch_t b);
 void lpb_destroy(lpb_handle h);

@@ -172,6 +172,84 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
     return LPB_OK;
 }
 
+// Times R plain iterations (no check) of `count` copies of the base LP on the
+// handle's lane of its precision: per-iteration microseconds of the primal and
+// dual steps (medians over the iterations).
+template <typename T>
+lpb_err time_steps(lpb_ctx* h, int count, int R, double* us_primal, double* us_dual) {
+    lpb_err rc;
+    cudaStream_t s = h->stream;
+    Lane& ln = h->lane[prec_of<T>()];
+    if ((rc = lane_reserve(h, ln, prec_of<T>(), count, 1)) != LPB_OK) return rc;
+    if ((rc = ensure_check_ws(h, ln.cap)) != LPB_OK) return rc;
+    if ((rc = ensure_specs(h, count)) != LPB_OK) return rc;
+    std::vector<lpb_lp_spec> sp(count);
+    for (auto& q : sp) {
+        q.kind = 0;
+        q.var = -1;
+        q.lo = -HUGE_VAL;
+        q.hi = HUGE_VAL;
+        q.sign = 1.0;
+    }
+    CU(cudaMemcpyAsync(h->specs_dev, sp.data(), sizeof(lpb_lp_spec) * count, cudaMemcpyHostToDevice, s));
+    std::vector<lpb_lp_result> res(count);
+    GroupRun g;
+    g.id = 0;
+    g.count = count;
+    g.slot0 = 0;
+    g.max_iter = 1 << 30;
+    g.res = res.data();
+    std::vector<GroupRun*> groups(1, nullptr);
+    if ((rc = lane_admit<T>(h, ln, g, h->specs_dev, nullptr, nullptr, 0, 0, 1e-4, s, groups)) != LPB_OK) return rc;
+    const IterData<T> id = lane_iter_data<T>(h, ln);
+    const IterBufs<T> ib = lane_iter_bufs<T>(ln);
+    const T* hal = lane_hal<T>(ln);
+    cudaEvent_t ev[3];
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    std::vector<float> tp, td;
+    cudaError_t ce = cudaSuccess;
+    for (int t = 0; t < R + 2 && ce == cudaSuccess; ++t) {
+        ce = launch_iteration<T>(id, ib, ln.cap, ln.ncol, hal, t % h->opt.check_every, h->opt.check_every, 0, false,
+                                 false, s, ev);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        float a = 0.f, b = 0.f;
+        if (ce == cudaSuccess && t >= 2) {
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            tp.push_back(a);
+            td.push_back(b);
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    // leave the lane empty
+    ln.ncol = 0;
+    std::fill(ln.slot_used.begin(), ln.slot_used.end(), 0);
+    std::fill(ln.col_group.begin(), ln.col_group.end(), -1);
+    cudaMemsetAsync(ln.ctl, 0, sizeof(Control) * ln.gcap, s);
+    cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "timed steps");
+    std::sort(tp.begin(), tp.end());
+    std::sort(td.begin(), td.end());
+    *us_primal = 1e3 * tp[tp.size() / 2];
+    *us_dual = 1e3 * td[td.size() / 2];
+    return LPB_OK;
+}
+
+lpb_err time_steps_any(lpb_ctx* h, int count, int R, double* up, double* ud) {
+    return h->opt.precision == LPB_MIXED ? time_steps<float>(h, count, R, up, ud)
+                                         : time_steps<double>(h, count, R, up, ud);
+}
+
+lpb_err apply_shape(lpb_ctx* h, Csr& c, int thr, int shift) {
+    if (c.long_thr != thr) {
+        c.long_thr = thr;
+        CU(build_long_rows(c, h->stream));
+    }
+    c.g_shift = shift;
+    h->ws_epoch += 1;  // captured intervals hold the old launch shapes
+    return LPB_OK;
+}
+
 lpb_err solve_common(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs_dev, double tol, int64_t max_iter,
                      const double* wx, const double* wy, lpb_batch_t* out) {
     lpb_batch* bt = new (std::nothrow) lpb_batch();
@@ -228,6 +306,9 @@ void lpb_default_options(lpb_options* o) {
     o->fp64_polish = 1;
     o->polish_stall_checks = 32;
     o->polish_arith = LPB_POLISH_DFLOAT;
+    o->eps_dual = -1.0;
+    o->use_graphs = 1;
+    o->use_pdl = 1;
 }
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
@@ -361,8 +442,6 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
         CU(scale_values(h->At, h->At.v64, h->d_r, h->d_c, false, h->At.v64, h->At.v32, s));
         CU(build_long_rows(h->A, s));
         CU(build_long_rows(h->At, s));
-        if (h->A.long_rows) F.push_back(h->A.long_rows);
-        if (h->At.long_rows) F.push_back(h->At.long_rows);
         // scaled vectors
         CU(dmalloc(F, &h->cs, sizeof(double) * n));
         CU(dmalloc(F, &h->xls, sizeof(double) * n));
@@ -516,6 +595,118 @@ lpb_err lpb_result_device(lpb_batch_t b, const double** x_dev, const double** y_
     return LPB_OK;
 }
 
+lpb_err lpb_obbt_tighten(lpb_batch_t b, const lpb_lp_spec* specs, const double* var_lo, const double* var_hi,
+                         double min_gain, double* new_lo, double* new_hi, int32_t* updated) {
+    if (!b || !var_lo || !var_hi || !new_lo || !new_hi || (b->num_lps > 0 && !specs))
+        return fail(LPB_ERR_INVALID_ARG, "null argument");
+    if (!(min_gain >= 0.0)) return fail(LPB_ERR_INVALID_ARG, "min_gain must be >= 0");
+    const int n = b->n;
+    for (int j = 0; j < n; ++j) {
+        new_lo[j] = var_lo[j];
+        new_hi[j] = var_hi[j];
+    }
+    int32_t cnt = 0;
+    for (int q = 0; q < b->num_lps; ++q) {
+        const lpb_lp_spec& sp = specs[q];
+        const lpb_lp_result& r = b->res[q];
+        if (sp.kind != 2 || r.status != LPB_OPTIMAL || !std::isfinite(r.safe_bound)) continue;
+        if (sp.var < 0 || sp.var >= n) return fail(LPB_ERR_BAD_INDEX, "an override names a variable outside [0, n)");
+        const int j = sp.var;
+        if (sp.sign > 0.0) {
+            // min x_j >= safe_bound / sign
+            const double cand = r.safe_bound / sp.sign;
+            if (cand > new_lo[j] + min_gain && cand <= var_hi[j]) {
+                new_lo[j] = cand;
+                ++cnt;
+            }
+        } else if (sp.sign < 0.0) {
+            // min sign x_j >= safe_bound, so x_j <= safe_bound / sign
+            const double cand = r.safe_bound / sp.sign;
+            if (cand < new_hi[j] - min_gain && cand >= var_lo[j]) {
+                new_hi[j] = cand;
+                ++cnt;
+            }
+        }
+    }
+    if (updated) *updated = cnt;
+    return LPB_OK;
+}
+
+lpb_err lpb_get_tuning(lpb_handle h, lpb_tuning* t) {
+    if (!h || !t) return fail(LPB_ERR_INVALID_ARG, "null argument");
+    t->long_row_primal = h->At.long_thr;
+    t->long_row_dual = h->A.long_thr;
+    t->lane_shift_primal = h->At.g_shift;
+    t->lane_shift_dual = h->A.g_shift;
+    return LPB_OK;
+}
+
+lpb_err lpb_set_tuning(lpb_handle h, const lpb_tuning* t) {
+    if (!h || !t) return fail(LPB_ERR_INVALID_ARG, "null argument");
+    if (t->long_row_primal < 1 || t->long_row_dual < 1 || t->lane_shift_primal < 0 || t->lane_shift_primal > 5 ||
+        t->lane_shift_dual < 0 || t->lane_shift_dual > 5)
+        return fail(LPB_ERR_INVALID_ARG, "thresholds must be >= 1 and shifts in [0, 5]");
+    DeviceGuard guard(h->device);
+    lpb_err rc;
+    if ((rc = apply_shape(h, h->At, t->long_row_primal, t->lane_shift_primal)) != LPB_OK) return rc;
+    if ((rc = apply_shape(h, h->A, t->long_row_dual, t->lane_shift_dual)) != LPB_OK) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return LPB_OK;
+}
+
+lpb_err lpb_autotune(lpb_handle h, int32_t num_lps, lpb_tuning* chosen) {
+    if (!h) return fail(LPB_ERR_INVALID_ARG, "null handle");
+    if (num_lps < 1 || num_lps > 65536) return fail(LPB_ERR_INVALID_ARG, "num_lps must be in [1, 65536]");
+    DeviceGuard guard(h->device);
+    const int thrs[] = {8, 16, 32, 64, 128, 256};
+    double best_p = 1e300, best_d = 1e300;
+    int bp_thr = h->At.long_thr, bp_sh = h->At.g_shift, bd_thr = h->A.long_thr, bd_sh = h->A.g_shift;
+    lpb_err rc;
+    for (int thr : thrs) {
+        for (int sh = 0; sh <= 2; ++sh) {
+            // both steps take the candidate; each step keeps its own best
+            if ((rc = apply_shape(h, h->At, thr, sh)) != LPB_OK) return rc;
+            if ((rc = apply_shape(h, h->A, thr, sh)) != LPB_OK) return rc;
+            double up = 0.0, ud = 0.0;
+            if ((rc = time_steps_any(h, num_lps, 9, &up, &ud)) != LPB_OK) return rc;
+            if (up < best_p) {
+                best_p = up;
+                bp_thr = thr;
+                bp_sh = sh;
+            }
+            if (ud < best_d) {
+                best_d = ud;
+                bd_thr = thr;
+                bd_sh = sh;
+            }
+        }
+    }
+    lpb_tuning t{bp_thr, bd_thr, bp_sh, bd_sh};
+    if ((rc = lpb_set_tuning(h, &t)) != LPB_OK) return rc;
+    if (chosen) *chosen = t;
+    return LPB_OK;
+}
+
+lpb_err lpb_tune_batch(lpb_handle h, const int32_t* widths, int32_t count, double* us_per_iter, int32_t* best) {
+    if (!h || !widths || !us_per_iter || count < 1) return fail(LPB_ERR_INVALID_ARG, "null argument or count < 1");
+    for (int32_t i = 0; i < count; ++i)
+        if (widths[i] < 1 || widths[i] > 65536) return fail(LPB_ERR_INVALID_ARG, "widths must be in [1, 65536]");
+    DeviceGuard guard(h->device);
+    double best_rate = -1.0;
+    for (int32_t i = 0; i < count; ++i) {
+        double up = 0.0, ud = 0.0;
+        lpb_err rc = time_steps_any(h, widths[i], 9, &up, &ud);
+        if (rc != LPB_OK) return rc;
+        us_per_iter[i] = up + ud;
+        const double rate = widths[i] / (up + ud);
+        if (rate > best_rate) {
+            best_rate = rate;
+            if (best) *best = i;
+        }
+    }
+    return LPB_OK;
+}
+
 lpb_err lpb_batch_profile(lpb_batch_t b, lpb_profile* p) {
     if (!b || !p) return fail(LPB_ERR_INVALID_ARG, "null argument");
     *p = b->prof;
@@ -555,6 +746,8 @@ void lpb_destroy(lpb_handle h) {
     free_list(h->ws_allocs);
     if (h->specs_dev) cudaFree(h->specs_dev);
     free_list(h->fixed_allocs);
+    if (h->A.long_rows) cudaFree(h->A.long_rows);
+    if (h->At.long_rows) cudaFree(h->At.long_rows);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -76,7 +76,7 @@ struct SpmmArgs {
     const int* ci;
     const double* va;
     const int* long_rows;
-    int n_long;
+    int n_long, long_thr;
     const TX* s0;
     const TX* s1;
     const TX* s2;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm64(const SpmmArgs<TX> a) {
     } else {
         row = ((int)blockIdx.x - a.n_long) * GPB + grp;
         if (row >= a.rows) return;
-        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+        if (a.rp[row + 1] - a.rp[row] > a.long_thr) return;
     }
     double acc[NOPS][V];
 #pragma unroll
@@ -157,7 +157,7 @@ template <typename TX, int NOPS>
 cudaError_t spmm64(const Csr& m, const TX* s0, const TX* s1, const TX* s2, double* o0, double* o1, double* o2,
                    int ld, int ncol, cudaStream_t s) {
     if (m.rows == 0 || ncol == 0) return cudaSuccess;
-    SpmmArgs<TX> a{m.rows, m.rp, m.ci, m.v64, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
+    SpmmArgs<TX> a{m.rows, m.rp, m.ci, m.v64, m.long_rows, m.n_long, m.long_thr, s0, s1, s2, o0, o1, o2, ld, ncol};
     constexpr int V = Vec<TX>::V;
     const int vecs = (ncol + V - 1) / V;
     if (vecs <= 1) return spmm_g<TX, 1, NOPS>(a, s);
@@ -333,9 +333,8 @@ struct DecideArgs {
     float* hal32;
     dfloat* haldf;
     double* rscr;     // residual of each active LP at this check, by slot
-    int* rtag;        // == tag where rscr holds this check's value
-    int tag;
-    int* flags;       // [0]: some group restarted
+    int* rtag;        // == this check's tag where rscr holds this check's value
+    int* flags;       // [0]: some group restarted; [1]: check counter (the tag)
 };
 
 constexpr int kDecideThreads = 1024;
@@ -348,12 +347,18 @@ constexpr int kDecideThreads = 1024;
 template <typename T>
 __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a) {
     const size_t ld = (size_t)a.ld;
+    __shared__ int sh_tag;
     for (int g = threadIdx.x; g < a.gcap; g += blockDim.x) a.ctl[g].stalled = 0;
-    if (threadIdx.x == 0) a.flags[0] = 0;
+    if (threadIdx.x == 0) {
+        a.flags[0] = 0;
+        sh_tag = a.flags[1] + 1;
+        a.flags[1] = sh_tag;
+    }
     __syncthreads();
+    const int tag = sh_tag;
     for (int j = threadIdx.x; j < a.ncol; j += blockDim.x) {
         const int g = a.col.grp[j];
-        const double tol = a.ctl[g].tol, eps_inf = a.ctl[g].eps_inf;
+        const double tol = a.ctl[g].tol, eps_inf = a.ctl[g].eps_inf, tol_dual = a.ctl[g].tol_dual;
         double st[kNumStats];
         for (int s = 0; s < kNumStats; ++s) st[s] = a.colsum[s * ld + j];
         const double rel_p = sqrt(st[S_PRES2]) / (1.0 + sqrt(st[S_AX2]));
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         int status = -1;
         if (isnan(ctx) || isnan(dsum) || isnan(rel_p) || isnan(rel_d) || isnan(rel_g) || !isfinite(r)) {
             status = LPB_NUMERICAL;
-        } else if (rel_p <= tol && rel_d <= tol && rel_g <= tol) {
+        } else if (rel_p <= tol && rel_d <= tol_dual && rel_g <= tol) {
             status = LPB_OPTIMAL;
         } else if (a.detect_inf) {
             const double ph = st[S_PHIDY] + st[S_PHIDR];
@@ -386,11 +391,13 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         rc.rel_primal = rel_p;
         rc.rel_dual = rel_d;
         rc.rel_gap = rel_g;
+        // the dual bound shifted by Delta = tol (1 + |c^T x| + |phi + phi|) (Sec. 6, OBBT)
+        rc.safe = -dsum - tol * (1.0 + fabs(ctx) + fabs(dsum));
         a.rec[j] = rc;
         if (status < 0) {
             const int slot = a.col.slot[j];
             a.rscr[slot] = r;
-            a.rtag[slot] = a.tag;
+            a.rtag[slot] = tag;
             if (a.stall_checks > 0) {
                 // an LP stalls when its KKT error has not halved for stall_checks checks
                 const double err = fmax(rel_p, fmax(rel_d, rel_g));
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
         int cnt = 0;
         for (int q = lane; q < c->nslots; q += 32) {
             const int slot = c->slot0 + q;
-            if (a.rtag[slot] == a.tag) {
+            if (a.rtag[slot] == tag) {
                 sum += a.rscr[slot];
                 ++cnt;
             }
@@ -512,7 +519,8 @@ struct InitArgs {
 // A new restart group g owning residual slots [slot0, slot0 + nslots); runs
 // before k_init_columns, whose threads may raise ctl[g].error.
 __global__ void k_admit_group(Control* ctl, int g, int slot0, int nslots, double tol, double eps_inf,
-                              long long max_iter, double* hal64, float* hal32, dfloat* haldf, int ce) {
+                              double tol_dual, long long max_iter, double* hal64, float* hal32, dfloat* haldf,
+                              int ce) {
     if (threadIdx.x == 0) {
         Control c{};
         c.k = 0;
@@ -527,6 +535,7 @@ __global__ void k_admit_group(Control* ctl, int g, int slot0, int nslots, double
         c.max_iter = max_iter;
         c.tol = tol;
         c.eps_inf = eps_inf;
+        c.tol_dual = tol_dual;
         c.slot0 = slot0;
         c.nslots = nslots;
         c.active = 1;
@@ -605,7 +614,7 @@ __global__ void k_init_columns(const InitArgs<T> a) {
     rc.status = status;
     rc.pad = 0;
     rc.r = 0.0;
-    rc.obj = rc.dual_obj = rc.rel_primal = rc.rel_dual = rc.rel_gap = NAN;
+    rc.obj = rc.dual_obj = rc.rel_primal = rc.rel_dual = rc.rel_gap = rc.safe = NAN;
     a.rec[j] = rc;
 }
 
@@ -744,7 +753,7 @@ struct SpmmDfArgs {
     const float* vhi;   // A~ in double-float: vhi + vlo
     const float* vlo;
     const int* long_rows;
-    int n_long;
+    int n_long, long_thr;
     const TI* s0;
     const TI* s1;
     const TI* s2;
@@ -771,7 +780,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs<TI> a) {
     } else {
         row = ((int)blockIdx.x - a.n_long) * GPB + grp;
         if (row >= a.rows) return;
-        if (a.rp[row + 1] - a.rp[row] > kLongRow) return;
+        if (a.rp[row + 1] - a.rp[row] > a.long_thr) return;
     }
     df acc[NOPS][V];
 #pragma unroll
@@ -827,7 +836,8 @@ cudaError_t spmm_df(const Csr& m, const TI* s0, const TI* s1, const TI* s2, df* 
                     int ncol, cudaStream_t s) {
     if (m.rows == 0 || ncol == 0) return cudaSuccess;
     constexpr int V = Vec<TI>::V;
-    SpmmDfArgs<TI> a{m.rows, m.rp, m.ci, m.v32, m.v32lo, m.long_rows, m.n_long, s0, s1, s2, o0, o1, o2, ld, ncol};
+    SpmmDfArgs<TI> a{m.rows, m.rp,   m.ci, m.v32, m.v32lo, m.long_rows, m.n_long,
+                     m.long_thr, s0, s1, s2, o0,   o1,    o2,          ld,       ncol};
     const int vecs = (ncol + V - 1) / V;
     const int G = vecs <= 1 ? 1 : vecs <= 2 ? 2 : vecs <= 4 ? 4 : vecs <= 8 ? 8 : vecs <= 16 ? 16 : 32;
     const int gpb = kBlock / G, tn = G * V;
@@ -951,7 +961,7 @@ __global__ void k_reduce_n_df(const ReduceDfArgs<TI> a) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len, int tag,
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len,
                          double* P, double* Q, double* partials, double* colsum, ColRecord* rec, ColParams<T> colp,
                          cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
@@ -1085,7 +1095,6 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     da.haldf = d.haldf;
     da.rscr = d.rscr;
     da.rtag = d.rtag;
-    da.tag = tag;
     da.flags = d.flags;
     k_decide<T><<<1, kDecideThreads, 0, s>>>(da);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1104,7 +1113,8 @@ template <typename T>
 cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int c0, int count,
                          int group, int slot0, const lpb_lp_spec* specs_dev, const double* warm_x,
                          const double* warm_y, int64_t wsx, int64_t wsy, double c_norm_base, double b_norm,
-                         double tol, double eps_inf, int64_t max_iter, ColRecord* rec, cudaStream_t s) {
+                         double tol, double eps_inf, double tol_dual, int64_t max_iter, ColRecord* rec,
+                         cudaStream_t s) {
     InitArgs<T> a{};
     a.m = d.m;
     a.n = d.n;
@@ -1127,8 +1137,8 @@ cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBu
     a.colc = d.col;
     a.rec = rec;
     a.ctl = d.ctl;
-    k_admit_group<<<1, 256, 0, s>>>(d.ctl, group, slot0, count, tol, eps_inf, (long long)max_iter, d.hal64, d.hal32,
-                                    d.haldf, d.check_every);
+    k_admit_group<<<1, 256, 0, s>>>(d.ctl, group, slot0, count, tol, eps_inf, tol_dual, (long long)max_iter,
+                                    d.hal64, d.hal32, d.haldf, d.check_every);
     if (count <= 0) return cudaGetLastError();
     k_init_columns<T><<<(count + 255) / 256, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -1247,11 +1257,12 @@ cudaError_t launch_group_moved(const CheckData& dst, int group, int slot0, cudaS
 }
 
 #define LPB_INSTANTIATE(T)                                                                                        \
-    template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int, int, double*, double*,  \
+    template cudaError_t launch_check<T>(const CheckData&, const IterBufs<T>&, int, int, int, double*, double*,       \
                                          double*, double*, ColRecord*, ColParams<T>, cudaStream_t, cudaEvent_t*);     \
     template cudaError_t launch_admit<T>(const CheckData&, const IterData<T>&, const IterBufs<T>&, int, int, int,     \
                                          int, int, const lpb_lp_spec*, const double*, const double*, int64_t,         \
-                                         int64_t, double, double, double, double, int64_t, ColRecord*, cudaStream_t); \
+                                         int64_t, double, double, double, double, double, int64_t, ColRecord*,        \
+                                         cudaStream_t);                                                               \
     template cudaError_t launch_extract<T>(const CheckData&, const IterBufs<T>&, int, const int*, double* const*,     \
                                            int, const double*, const double*, cudaStream_t);                          \
     template cudaError_t launch_compact<T>(const IterBufs<T>&, int, int, int, const int*, const int*, int,            \

@@ -83,6 +83,7 @@ void set_result(lpb_lp_result& r, const ColRecord& rc, int status, int64_t iters
     r.rel_primal = rc.rel_primal;
     r.rel_dual = rc.rel_dual;
     r.rel_gap = rc.rel_gap;
+    r.safe_bound = rc.safe;
 }
 
 // Removes the columns `gone` (ascending) from the lane by moving live tail
@@ -149,6 +150,8 @@ bool polish_enabled(const lpb_ctx* h) { return h->opt.precision == LPB_MIXED && 
 bool polish_dfloat(const lpb_ctx* h) { return polish_enabled(h) && h->opt.polish_arith == LPB_POLISH_DFLOAT; }
 
 void lane_free(Lane& ln) {
+    if (ln.exec) cudaGraphExecDestroy(ln.exec);
+    ln.exec = nullptr;
     for (void* p : ln.allocs) cudaFree(p);
     ln.allocs.clear();
     if (ln.rec_h) cudaFreeHost(ln.rec_h);
@@ -203,7 +206,6 @@ lpb_err lane_reserve(lpb_ctx* h, Lane& ln, int prec, int cap, int gcap) {
     ln.cap = cap;
     ln.gcap = gcap;
     ln.ncol = 0;
-    ln.tag = 0;
     ln.col_group.assign(cap, -1);
     ln.col_lp.assign(cap, -1);
     ln.slot_used.assign(nslot, 0);
@@ -222,6 +224,7 @@ lpb_err ensure_check_ws(lpb_ctx* h, int cap) {
     LPB_CU(dmalloc(L, &h->partials, sizeof(double) * (size_t)kNumStats * kReduceBlocks * cap));
     LPB_CU(dmalloc(L, &h->colsum, sizeof(double) * (size_t)kNumStats * cap));
     h->ws_cap = cap;
+    h->ws_epoch += 1;  // captured intervals hold the old workspace pointers
     return LPB_OK;
 }
 
@@ -336,9 +339,10 @@ lpb_err lane_admit(lpb_ctx* h, Lane& ln, GroupRun& g, const lpb_lp_spec* specs_d
     if (g.id < 0 || g.id >= ln.gcap) return fail(LPB_ERR_INVALID_ARG, "bad group id");
     if (g.slot0 < 0 || g.slot0 + count > (int)ln.slot_used.size()) return fail(LPB_ERR_INVALID_ARG, "bad slots");
     const double eps_inf = h->opt.eps_infeas >= 0.0 ? h->opt.eps_infeas : tol;
+    const double tol_dual = h->opt.eps_dual >= 0.0 ? h->opt.eps_dual : tol;
     const CheckData cd = lane_check_data(h, ln, 0);
     LPB_CU(launch_admit<T>(cd, iter_data<T>(h, ln), iter_bufs<T>(ln), ln.cap, c0, count, g.id, g.slot0, specs_dev, wx,
-                           wy, wsx, wsy, h->c_norm_base, h->b_norm, tol, eps_inf, g.max_iter, ln.rec, s));
+                           wy, wsx, wsy, h->c_norm_base, h->b_norm, tol, eps_inf, tol_dual, g.max_iter, ln.rec, s));
     if (count > 0)
         LPB_CU(cudaMemcpyAsync(ln.rec_h + c0, ln.rec + c0, sizeof(ColRecord) * count, cudaMemcpyDeviceToHost, s));
     LPB_CU(cudaMemcpyAsync(ln.ctl_h + g.id, ln.ctl + g.id, sizeof(Control), cudaMemcpyDeviceToHost, s));
@@ -380,21 +384,73 @@ lpb_err lane_admit(lpb_ctx* h, Lane& ln, GroupRun& g, const lpb_lp_spec* specs_d
     return LPB_OK;
 }
 
+// The work of one interval queued on stream s: L iterations, the check, the
+// copies of the per-column and per-group records.
 template <typename T>
-lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, lpb_profile* prof) {
-    const int m = h->m, ld = ln.cap, ce = h->opt.check_every;
+lpb_err queue_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, int uni, bool timed, cudaStream_t s) {
+    const int ld = ln.cap, ce = h->opt.check_every;
     const IterData<T> id = iter_data<T>(h, ln);
     const IterBufs<T> ib = iter_bufs<T>(ln);
     const CheckData cd = lane_check_data(h, ln, stall_checks);
-    const bool timed = prof && h->opt.profile && (int)h->events.size() >= 3 * ce + 3;
     const T* hal = pick<T>(ln.hal64, ln.hal32, ln.haldf);
+    const bool pdl = h->opt.use_pdl != 0;
+    for (int t = 0; t < L; ++t)
+        LPB_CU(launch_iteration<T>(id, ib, ld, ln.ncol, hal, t, ce, uni, t == L - 1, pdl, s,
+                                   timed ? &h->events[3 * t] : nullptr));
+    LPB_CU(launch_check<T>(cd, ib, ld, ln.ncol, L, h->P, h->Q, h->partials, h->colsum, ln.rec, id.col, s,
+                           timed ? &h->events[3 * L] : nullptr));
+    LPB_CU(cudaMemcpyAsync(ln.rec_h, ln.rec, sizeof(ColRecord) * ln.ncol, cudaMemcpyDeviceToHost, s));
+    LPB_CU(cudaMemcpyAsync(ln.ctl_h, ln.ctl, sizeof(Control) * ln.gcap, cudaMemcpyDeviceToHost, s));
+    return LPB_OK;
+}
+
+template <typename T>
+lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, lpb_profile* prof) {
+    const int m = h->m, ce = h->opt.check_every;
+    const bool timed = prof && h->opt.profile && (int)h->events.size() >= 3 * ce + 3;
     int uni = ln.ncol > 0 ? ln.col_group[0] : -1;
     for (int j = 1; j < ln.ncol && uni >= 0; ++j)
         if (ln.col_group[j] != uni) uni = -1;
+    if (!h->opt.use_graphs || timed) {
+        lpb_err rc = queue_interval<T>(h, ln, L, stall_checks, uni, timed, s);
+        if (rc != LPB_OK) return rc;
+    } else {
+        // one CUDA graph per interval shape, replayed while the shape holds;
+        // a new shape updates the executable graph in place when it can
+        const GraphKey key{ln.ncol, uni, L, stall_checks, h->ws_epoch, (int)(sizeof(T))};
+        if (!ln.exec || !(ln.gkey == key)) {
+            cudaGraph_t g = nullptr;
+            LPB_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const lpb_err rc = queue_interval<T>(h, ln, L, stall_checks, uni, false, s);
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (rc != LPB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            LPB_CU(e);
+            if (ln.exec) {
+                cudaGraphExecUpdateResultInfo info{};
+                if (cudaGraphExecUpdate(ln.exec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(ln.exec);
+                    ln.exec = nullptr;
+                }
+            }
+            if (!ln.exec) {
+                const cudaError_t ei = cudaGraphInstantiate(&ln.exec, g, 0);
+                if (ei != cudaSuccess) {
+                    cudaGraphDestroy(g);
+                    ln.exec = nullptr;
+                    return cuda_fail(ei, "cudaGraphInstantiate");
+                }
+            }
+            cudaGraphDestroy(g);
+            ln.gkey = key;
+        }
+        LPB_CU(cudaGraphLaunch(ln.exec, s));
+    }
     for (int t = 0; t < L; ++t) {
         const bool chk = t == L - 1;
-        LPB_CU(launch_iteration<T>(id, ib, ld, ln.ncol, hal, t, ce, uni, chk, s,
-                                   timed ? &h->events[3 * t] : nullptr));
         if (prof) {
             prof->launches[0] += 1;
             prof->launches[1] += m > 0 ? 1 : 0;
@@ -403,17 +459,12 @@ lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_
             prof->bytes[1] += step_bytes(prec_of<T>(), h->nnz, m, h->n, false, chk, ln.ncol);
         }
     }
-    ln.tag += 1;
-    LPB_CU(launch_check<T>(cd, ib, ld, ln.ncol, L, ln.tag, h->P, h->Q, h->partials, h->colsum, ln.rec, id.col, s,
-                           timed ? &h->events[3 * L] : nullptr));
     if (prof) {
         prof->launches[2] += m > 0 ? 2 : 1;
         prof->launches[3] += 1;
         prof->checks += 1;
         prof->kernels += (m > 0 ? 2 : 1) + (m > 0 ? 1 : 0) + 1 + 1 + 1 + (m > 0 ? 2 : 1);
     }
-    LPB_CU(cudaMemcpyAsync(ln.rec_h, ln.rec, sizeof(ColRecord) * ln.ncol, cudaMemcpyDeviceToHost, s));
-    LPB_CU(cudaMemcpyAsync(ln.ctl_h, ln.ctl, sizeof(Control) * ln.gcap, cudaMemcpyDeviceToHost, s));
     return LPB_OK;
 }
 
@@ -514,11 +565,18 @@ lpb_err lane_migrate(lpb_ctx* h, Lane& src, Lane& dst, GroupRun& g, int id_dst, 
     return LPB_OK;
 }
 
+template <typename T> IterData<T> lane_iter_data(const lpb_ctx* h, const Lane& ln) { return iter_data<T>(h, ln); }
+template <typename T> IterBufs<T> lane_iter_bufs(const Lane& ln) { return iter_bufs<T>(ln); }
+template <typename T> const T* lane_hal(const Lane& ln) { return pick<T>(ln.hal64, ln.hal32, ln.haldf); }
+
 #define LPB_ENGINE_INSTANTIATE(T)                                                                                  \
     template lpb_err lane_admit<T>(lpb_ctx*, Lane&, GroupRun&, const lpb_lp_spec*, const double*, const double*,  \
                                    int64_t, int64_t, double, cudaStream_t, std::vector<GroupRun*>&);               \
     template lpb_err lane_interval<T>(lpb_ctx*, Lane&, int, int, cudaStream_t, lpb_profile*);                      \
-    template lpb_err lane_collect<T>(lpb_ctx*, Lane&, std::vector<GroupRun*>&, cudaStream_t, lpb_profile*);
+    template lpb_err lane_collect<T>(lpb_ctx*, Lane&, std::vector<GroupRun*>&, cudaStream_t, lpb_profile*);          \
+    template IterData<T> lane_iter_data<T>(const lpb_ctx*, const Lane&);                                            \
+    template IterBufs<T> lane_iter_bufs<T>(const Lane&);                                                            \
+    template const T* lane_hal<T>(const Lane&);
 LPB_ENGINE_INSTANTIATE(float)
 LPB_ENGINE_INSTANTIATE(double)
 LPB_ENGINE_INSTANTIATE(dfloat)

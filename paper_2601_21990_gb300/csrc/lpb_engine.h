@@ -27,6 +27,15 @@ namespace lpb {
 
 enum LanePrec { kPrecF32 = 0, kPrecF64 = 1, kPrecDfl = 2 };
 
+// what an interval's captured graph depends on besides the lane's buffers
+struct GraphKey {
+    int ncol = -1, uni = -1, L = -1, stall = -1, ws_epoch = -1, tsize = 0;
+    bool operator==(const GraphKey& o) const {
+        return ncol == o.ncol && uni == o.uni && L == o.L && stall == o.stall && ws_epoch == o.ws_epoch &&
+               tsize == o.tsize;
+    }
+};
+
 struct Lane {
     int prec = kPrecF32;
     int cap = 0;    // columns (= leading dimension of the iterate blocks)
@@ -54,9 +63,11 @@ struct Lane {
     int* mv_h = nullptr;
     double** optr_h = nullptr;
     std::vector<void*> allocs;
+    // the interval as an executable CUDA graph, for the shape gkey
+    cudaGraphExec_t exec = nullptr;
+    GraphKey gkey;
     // host bookkeeping
     int ncol = 0;
-    int tag = 0;                    // check counter (residual slot tags)
     std::vector<int> col_group;     // column -> group id
     std::vector<int> col_lp;        // column -> LP index within its group
     std::vector<char> slot_used;    // residual slots in use
@@ -103,6 +114,7 @@ struct lpb_ctx {
     lpb::Lane lane[3];
     // check workspace shared by the handle's lanes (they run on one stream)
     int ws_cap = 0;
+    int ws_epoch = 0;
     double *P = nullptr, *Q = nullptr, *partials = nullptr, *colsum = nullptr;
     lpb_lp_spec* specs_dev = nullptr;
     int specs_cap = 0;
@@ -138,6 +150,9 @@ int lane_find_slots(const Lane& ln, int count);
 int lane_free_group(const Lane& ln, const std::vector<GroupRun*>& groups);
 
 CheckData lane_check_data(const lpb_ctx* h, const Lane& ln, int stall_checks);
+template <typename T> IterData<T> lane_iter_data(const lpb_ctx* h, const Lane& ln);
+template <typename T> IterBufs<T> lane_iter_bufs(const Lane& ln);
+template <typename T> const T* lane_hal(const Lane& ln);
 
 // Admits a group of g.count LPs at columns [ln.ncol, ln.ncol + count); LPs
 // that are infeasible from their overrides alone finish at once.  Synchronizes.

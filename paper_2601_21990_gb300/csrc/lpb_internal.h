@@ -61,8 +61,10 @@ struct Csr {
     double* v64 = nullptr;      // scaled values, FP64
     float* v32 = nullptr;       // scaled values, FP32 (mixed path)
     float* v32lo = nullptr;     // v64 - v32 rounded to FP32: (v32, v32lo) is v64 in double-float
-    int* long_rows = nullptr;   // rows with > kLongRow entries
+    int* long_rows = nullptr;   // rows with > long_thr entries
     int n_long = 0;
+    int long_thr = kLongRow;    // rows longer than this get a whole block (tunable)
+    int g_shift = 0;            // step kernels use (lanes per row from the batch width) >> g_shift
 };
 
 // Per-column parameters of the iteration kernels (structure of arrays,
@@ -99,6 +101,7 @@ struct ColRecord {
     int pad;
     double r;     // fixed-point residual (scaled, M-norm)
     double obj, dual_obj, rel_primal, rel_dual, rel_gap;
+    double safe;  // dual_obj - tol (1 + |obj| + |dual_obj|)
 };
 
 // State of one restart group on the device.  A group is the set of LPs
@@ -117,7 +120,7 @@ struct Control {
     int64_t restarts;
     int64_t K;        // iterations the group has run
     int64_t max_iter;
-    double tol, eps_inf;
+    double tol, eps_inf, tol_dual;
     int slot0, nslots;  // the group's LPs own residual slots [slot0, slot0 + nslots)
     int active;
     int pad;
@@ -131,6 +134,7 @@ void set_last_error(const char* msg);
 // ---------------------------------------------------------------------------
 cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm_out, cudaStream_t s);
 cudaError_t exclusive_scan_i32(const int* in, int* out, int count, int* total_dev, cudaStream_t s);
+// (re)builds a.long_rows for threshold a.long_thr (frees an old list)
 cudaError_t build_long_rows(Csr& a, cudaStream_t s);
 cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& at, const double* at_vals,
                                 int ruiz_iters, int pock_chambolle, double* d_r, double* d_c,
@@ -175,10 +179,12 @@ struct IterData {
 // hal[2 (g ce + t)], hal[2 (g ce + t) + 1] are the Halpern weights
 // (k+1)/(k+2), 1/(k+2) of Eq. mainiter for iteration t of the interval of
 // restart group g (ce = check_every), written on the device by the checks.
-// uni >= 0 says that every active column belongs to group uni.
+// uni >= 0 says that every active column belongs to group uni.  With pdl
+// the step kernels after the interval's first are programmatic dependents of
+// their predecessor (not with timing events, which sit between them).
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol,
-                             const T* hal, int t, int ce, int uni, bool check, cudaStream_t s,
+                             const T* hal, int t, int ce, int uni, bool check, bool pdl, cudaStream_t s,
                              cudaEvent_t* ev /* 3 events or nullptr */);
 
 // ---------------------------------------------------------------------------
@@ -202,8 +208,8 @@ struct CheckData {
     float* hal32;                  //   [gcap][check_every][2], in each iterate type
     dfloat* haldf;
     double* rscr;                  // per-LP residual slots of the averaged restart test
-    int* rtag;
-    int* flags;                    // [0]: a group restarted at the last check
+    int* rtag;                     // slot holds this check's value where rtag == the check's tag
+    int* flags;                    // [0]: a group restarted at the last check; [1]: checks so far
     // double-float copies for the FP32-iterate checks: scalings, their
     // reciprocals, original c, xlo, xhi (n) and l, u (m)
     const df *f_dr, *f_dc, *f_idr, *f_idc, *f_c, *f_xl, *f_xu, *f_l, *f_u;
@@ -213,7 +219,7 @@ struct CheckData {
 // FP64-accurate KKT statistics, per-LP status, then each restart group's
 // averaged restart test and primal-weight update and the anchor copies.
 template <typename T>
-cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len, int tag,
+cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int ncol, int interval_len,
                          double* P, double* Q, double* partials, double* colsum, ColRecord* rec, ColParams<T> colp,
                          cudaStream_t s, cudaEvent_t* ev /* 3 events or nullptr */);
 
@@ -226,7 +232,8 @@ template <typename T>
 cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBufs<T>& b, int ld, int c0, int count,
                          int group, int slot0, const lpb_lp_spec* specs_dev, const double* warm_x,
                          const double* warm_y, int64_t wsx, int64_t wsy, double c_norm_base, double b_norm,
-                         double tol, double eps_inf, int64_t max_iter, ColRecord* rec, cudaStream_t s);
+                         double tol, double eps_inf, double tol_dual, int64_t max_iter, ColRecord* rec,
+                         cudaStream_t s);
 
 // x, y of the finished columns cols_dev[f] in the original space, written to
 // outp_dev[f] (n values) and outp_dev[count + f] (m values); null pointers skip.

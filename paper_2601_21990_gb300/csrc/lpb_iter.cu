@@ -33,6 +33,10 @@
 #ifndef LPB_STEP_MIN_BLOCKS
 #define LPB_STEP_MIN_BLOCKS 5
 #endif
+// gathers a lane issues before it consumes them (loads in flight per lane)
+#ifndef LPB_GATHER_BATCH
+#define LPB_GATHER_BATCH 4
+#endif
 
 namespace lpb {
 
@@ -132,32 +136,30 @@ __device__ __forceinline__ void gather_round(const int (&c)[Round<T, G>::K], con
                                              const T* __restrict__ src, int ld, int colg, unsigned gmask,
                                              T (&acc)[V]) {
     constexpr int R = Round<T, G>::R;
+    constexpr int B = LPB_GATHER_BATCH < R ? LPB_GATHER_BATCH : R;
+    static_assert(R % B == 0, "a round is a whole number of gather batches");
     const int cfirst = __shfl_sync(gmask, c[0], 0, G);
 #pragma unroll
-    for (int k0 = 0; k0 < R; k0 += 4) {
+    for (int k0 = 0; k0 < R; k0 += B) {
         if (k0 >= cnt) break;
-        int cc[4];
-        T aa[4];
+        int cc[B];
+        T aa[B];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < B; ++j) {
             const int k = k0 + j;
             const int cs = __shfl_sync(gmask, c[k / G], k % G, G);
             const T as = shfl(gmask, a[k / G], k % G, G);
             cc[j] = k < cnt ? cs : cfirst;
             aa[j] = k < cnt ? as : T(0);
         }
-        T x0[V], x1[V], x2[V], x3[V];
-        ldg_v(src + (size_t)cc[0] * ld + colg, x0);
-        ldg_v(src + (size_t)cc[1] * ld + colg, x1);
-        ldg_v(src + (size_t)cc[2] * ld + colg, x2);
-        ldg_v(src + (size_t)cc[3] * ld + colg, x3);
+        T xs[B][V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            acc[v] = mad(aa[0], x0[v], acc[v]);
-            acc[v] = mad(aa[1], x1[v], acc[v]);
-            acc[v] = mad(aa[2], x2[v], acc[v]);
-            acc[v] = mad(aa[3], x3[v], acc[v]);
-        }
+        for (int j = 0; j < B; ++j) ldg_v(src + (size_t)cc[j] * ld + colg, xs[j]);
+        // entries in order, so a column's sum does not depend on G
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = mad(aa[j], xs[j][v], acc[v]);
     }
 }
 
@@ -183,7 +185,7 @@ struct StepArgs {
     const int* ci;
     const T* va;
     const int* long_rows;
-    int n_long;
+    int n_long, long_thr;
     const T* src;     // gathered block: Y^k (primal) or Xbar (dual)
     // row-side state
     T* Z;             // X^k -> X^{k+1} (primal) / Y^k -> Y^{k+1} (dual), in place
@@ -200,6 +202,7 @@ struct StepArgs {
     const T* hal;     // per group g: (k+1)/(k+2), 1/(k+2) of Eq. mainiter at [2 (g ce + t)]
     int t, ce;
     int uni;          // the group of every active column, or -1 if they belong to several
+    int pdl;          // launched as a programmatic dependent of the previous step kernel
 };
 
 // Reduce the row groups' partial sums of a long row through shared memory;
@@ -343,6 +346,15 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
         }
     }
     __syncthreads();
+    // Programmatic dependent launch: everything above reads only data that
+    // the previous kernel does not write (per-column parameters, Halpern
+    // weights); wait for it to complete before touching the iterates, then
+    // let the next step kernel start its own prologue on the SMs this grid
+    // frees.
+    if (a.pdl) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
     // one restart group in the whole batch: its Halpern weights as scalars
     const int hu = a.uni >= 0 ? 2 * (a.uni * a.ce + a.t) : 0;
     const T uca = a.uni >= 0 ? a.hal[hu] : T(0), ucb = a.uni >= 0 ? a.hal[hu + 1] : T(0);
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
     if (r < a.rows) {
         beg = a.rp[r];
         end = a.rp[r + 1];
-        load_round<T, G>(a.ci, a.va, beg, end - beg <= kLongRow ? end : beg, c, av);
+        load_round<T, G>(a.ci, a.va, beg, end - beg <= a.long_thr ? end : beg, c, av);
     }
 #pragma unroll 1
     while (r < a.rows) {
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
             nbeg = a.rp[rn];
             nend = a.rp[rn + 1];
         }
-        const bool is_short = end - beg <= kLongRow;
+        const bool is_short = end - beg <= a.long_thr;
         T acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = T(0);
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const Step
                 gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg + R, end, gmask, acc);
         }
         // the next row's first index round, issued before this row's epilogue
-        if (rn < a.rows) load_round<T, G>(a.ci, a.va, nbeg, nend - nbeg <= kLongRow ? nend : nbeg, c, av);
+        if (rn < a.rows) load_round<T, G>(a.ci, a.va, nbeg, nend - nbeg <= a.long_thr ? nend : nbeg, c, av);
         if (is_short && active) {
             if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc, uca, ucb);
             else dual_epilogue<T, V, TN, CHECK>(a, P, r, col0, lane * V, acc, uca, ucb);
@@ -422,8 +434,21 @@ cudaError_t launch_k(const StepArgs<T>& a, cudaStream_t s) {
     const int need = (a.rows + GPB - 1) / GPB;
     const int persist = need < sms * per_sm ? need : sms * per_sm;
     dim3 grid(a.n_long + persist, (a.ncol + TN - 1) / TN);
-    k_step<T, G, CHECK, PRIMAL><<<grid, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    if (!a.pdl) {
+        k_step<T, G, CHECK, PRIMAL><<<grid, kBlock, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step<T, G, CHECK, PRIMAL>, a);
 }
 
 template <typename T, int G>
@@ -434,9 +459,12 @@ cudaError_t launch_step(bool primal, bool check, const StepArgs<T>& a, cudaStrea
 }
 
 template <typename T>
-cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, cudaStream_t s) {
+cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, int g_shift, cudaStream_t s) {
     constexpr int V = Vec<T>::V;
-    const int vecs = (a.ncol + V - 1) / V;
+    // lanes per row group from the batch width, optionally narrowed (more
+    // column tiles, each row's gathers split over more blocks)
+    int vecs = (a.ncol + V - 1) / V;
+    for (int q = 0; q < g_shift && vecs > 1; ++q) vecs = (vecs + 1) / 2;
     if (vecs <= 1) return launch_step<T, 1>(primal, check, a, s);
     if (vecs <= 2) return launch_step<T, 2>(primal, check, a, s);
     if (vecs <= 4) return launch_step<T, 4>(primal, check, a, s);
@@ -449,7 +477,7 @@ cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, cudaStr
 
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol, const T* hal, int t,
-                             int ce, int uni, bool check, cudaStream_t s, cudaEvent_t* ev) {
+                             int ce, int uni, bool check, bool pdl, cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
     StepArgs<T> p{};
     p.rows = d.At.rows;
@@ -458,6 +486,7 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.va = d.at_vals;
     p.long_rows = d.At.long_rows;
     p.n_long = d.At.n_long;
+    p.long_thr = d.At.long_thr;
     p.src = b.Y;
     p.Z = b.X;
     p.Z0 = b.X0;
@@ -475,8 +504,10 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.t = t;
     p.ce = ce;
     p.uni = uni;
+    // the first primal step of an interval follows the check's copies
+    p.pdl = pdl && t > 0 && !ev;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    if ((e = dispatch_step<T>(true, check, p, s)) != cudaSuccess) return e;
+    if ((e = dispatch_step<T>(true, check, p, d.At.g_shift, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
 
     StepArgs<T> q{};
@@ -486,6 +517,7 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.va = d.a_vals;
     q.long_rows = d.A.long_rows;
     q.n_long = d.A.n_long;
+    q.long_thr = d.A.long_thr;
     q.src = b.Xbar;
     q.Z = b.Y;
     q.Z0 = b.Y0;
@@ -503,16 +535,17 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.t = t;
     q.ce = ce;
     q.uni = uni;
-    if ((e = dispatch_step<T>(false, check, q, s)) != cudaSuccess) return e;
+    q.pdl = pdl && !ev;
+    if ((e = dispatch_step<T>(false, check, q, d.A.g_shift, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 template cudaError_t launch_iteration<float>(const IterData<float>&, const IterBufs<float>&, int, int, const float*,
-                                             int, int, int, bool, cudaStream_t, cudaEvent_t*);
+                                             int, int, int, bool, bool, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_iteration<double>(const IterData<double>&, const IterBufs<double>&, int, int,
-                                              const double*, int, int, int, bool, cudaStream_t, cudaEvent_t*);
+                                              const double*, int, int, int, bool, bool, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_iteration<dfloat>(const IterData<dfloat>&, const IterBufs<dfloat>&, int, int,
-                                              const dfloat*, int, int, int, bool, cudaStream_t, cudaEvent_t*);
+                                              const dfloat*, int, int, int, bool, bool, cudaStream_t, cudaEvent_t*);
 
 }  // namespace lpb

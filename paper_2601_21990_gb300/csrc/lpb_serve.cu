@@ -78,6 +78,10 @@ struct lpb_server {
     std::string fatal_msg;
     std::vector<std::unique_ptr<Matrix>> mats;
     std::map<int64_t, std::unique_ptr<Request>> reqs;
+    // released result buffers, freed by the worker between intervals: only
+    // the worker enqueues work on the matrices' streams, which it captures
+    // into CUDA graphs (an enqueue from another thread would join a capture)
+    std::vector<std::pair<int, void*>> to_free;
     int64_t next_id = 0;
     int64_t budget = 0, used = 0;
     lpb_server_stats st{};
@@ -316,10 +320,13 @@ lpb_err step(lpb_server* srv, bool& did_work, bool& in_flight) {
     did_work = false;
     in_flight = false;
     std::vector<Matrix*> mats;
+    std::vector<std::pair<int, void*>> frees;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         for (auto& mp : srv->mats) mats.push_back(mp.get());
+        frees.swap(srv->to_free);
     }
+    for (const auto& f : frees) LPB_CU(cudaFreeAsync(f.second, mats[f.first]->h->stream));
     lpb_server_stats add{};
     lpb_profile prof{};
     lpb_err rc;
@@ -623,9 +630,11 @@ lpb_err lpb_server_release(lpb_server_t srv, int64_t id) {
     for (auto& mp : srv->mats)
         for (const Request* p : mp->pending)
             if (p->warm_request == id) return fail(LPB_ERR_INVALID_ARG, "a pending request warm-starts from it");
-    cudaSetDevice(srv->device);
-    free_request_results(r, srv->mats[r.matrix]->h->stream);
+    if (r.x_dev) srv->to_free.emplace_back(r.matrix, r.x_dev);
+    if (r.y_dev) srv->to_free.emplace_back(r.matrix, r.y_dev);
+    r.x_dev = r.y_dev = nullptr;
     r.released = true;
+    srv->cv_work.notify_all();
     if (r.charged) srv->used -= r.footprint;
     r.charged = false;
     srv->st.hbm_used_bytes = srv->used;
@@ -659,6 +668,11 @@ void lpb_server_destroy(lpb_server_t srv) {
         cudaStream_t s = srv->mats[kv.second->matrix]->h->stream;
         free_request_dev(*kv.second, s);
         free_request_results(*kv.second, s);
+        cudaStreamSynchronize(s);
+    }
+    for (const auto& f : srv->to_free) {
+        cudaStream_t s = srv->mats[f.first]->h->stream;
+        cudaFreeAsync(f.second, s);
         cudaStreamSynchronize(s);
     }
     delete srv;

@@ -190,9 +190,9 @@ __global__ void k_finish_transpose(const int* __restrict__ rp, int rows, const i
 // ---------------------------------------------------------------------------
 // long-row lists
 // ---------------------------------------------------------------------------
-__global__ void k_long_flags(const int* __restrict__ rp, int rows, int* __restrict__ flag) {
+__global__ void k_long_flags(const int* __restrict__ rp, int rows, int thr, int* __restrict__ flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
-        flag[i] = (rp[i + 1] - rp[i]) > kLongRow ? 1 : 0;
+        flag[i] = (rp[i + 1] - rp[i]) > thr ? 1 : 0;
 }
 
 __global__ void k_long_scatter(const int* __restrict__ flag, const int* __restrict__ pos, int rows,
@@ -441,13 +441,18 @@ cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm
 
 cudaError_t build_long_rows(Csr& a, cudaStream_t s) {
     cudaError_t e;
+    if (a.long_rows) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        cudaFree(a.long_rows);
+        a.long_rows = nullptr;
+    }
     a.n_long = 0;
     if (a.rows == 0) return cudaSuccess;
     int *flag = nullptr, *total = nullptr;
     if ((e = cudaMallocAsync((void**)&flag, sizeof(int) * ((size_t)a.rows * 2 + 1), s)) != cudaSuccess) return e;
     int* pos = flag + a.rows;
     total = pos + a.rows;
-    k_long_flags<<<grid_for(a.rows, 256), 256, 0, s>>>(a.rp, a.rows, flag);
+    k_long_flags<<<grid_for(a.rows, 256), 256, 0, s>>>(a.rp, a.rows, a.long_thr, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = exclusive_scan_i32(flag, pos, a.rows, total, s)) != cudaSuccess) return e;
     int h_total = 0;

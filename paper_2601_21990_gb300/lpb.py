@@ -30,7 +30,8 @@ POLISH_DFLOAT, POLISH_FP64 = 0, 1
 # every symbol include/lpb.h declares
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
            "lpb_result_device", "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_batch_free",
-           "lpb_destroy", "lpb_last_error", "lpb_scaling_noalloc"]
+           "lpb_destroy", "lpb_last_error", "lpb_scaling_noalloc", "lpb_obbt_tighten", "lpb_get_tuning",
+           "lpb_set_tuning", "lpb_autotune", "lpb_tune_batch"]
 # every symbol include/lpb_serve.h declares
 SERVE_EXPORTS = ["lpb_server_default_options", "lpb_server_create", "lpb_server_attach", "lpb_server_submit",
                  "lpb_server_poll", "lpb_server_wait", "lpb_server_result", "lpb_server_results",
@@ -52,7 +53,8 @@ class Options(C.Structure):
                 ("power_tol", C.c_double), ("power_seed", C.c_uint64), ("eps_infeas", C.c_double),
                 ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32),
-                ("polish_arith", C.c_int32)]
+                ("polish_arith", C.c_int32), ("eps_dual", C.c_double), ("use_graphs", C.c_int32),
+                ("use_pdl", C.c_int32)]
 
 
 class Spec(C.Structure):
@@ -63,13 +65,18 @@ class Spec(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("restarts", C.c_int32), ("iters", C.c_int64), ("obj", C.c_double),
                 ("dual_obj", C.c_double), ("rel_primal", C.c_double), ("rel_dual", C.c_double),
-                ("rel_gap", C.c_double)]
+                ("rel_gap", C.c_double), ("safe_bound", C.c_double)]
 
 
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("bytes", C.c_double * 4),
                 ("setup_ms", C.c_double), ("checks", C.c_int64), ("compactions", C.c_int64),
                 ("kernels", C.c_int64), ("fp64_switch_iter", C.c_int64)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("long_row_primal", C.c_int32), ("long_row_dual", C.c_int32), ("lane_shift_primal", C.c_int32),
+                ("lane_shift_dual", C.c_int32)]
 
 
 class ServerOptions(C.Structure):
@@ -129,6 +136,14 @@ def load(path: str = LIB_PATH):
     lib.lpb_destroy.restype = None
     lib.lpb_last_error.restype = C.c_char_p
     lib.lpb_scaling_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.lpb_obbt_tighten.argtypes = [vp, vp, vp, vp, d, vp, vp, C.POINTER(i32)]
+    lib.lpb_obbt_tighten.restype = C.c_int
+    lib.lpb_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    lib.lpb_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    lib.lpb_autotune.argtypes = [vp, i32, C.POINTER(Tuning)]
+    lib.lpb_tune_batch.argtypes = [vp, vp, i32, vp, C.POINTER(i32)]
+    for f in ("lpb_get_tuning", "lpb_set_tuning", "lpb_autotune", "lpb_tune_batch"):
+        getattr(lib, f).restype = C.c_int
     lib.lpb_server_default_options.argtypes = [C.POINTER(ServerOptions)]
     lib.lpb_server_default_options.restype = None
     lib.lpb_server_create.argtypes = [C.POINTER(ServerOptions), C.POINTER(vp)]
@@ -253,6 +268,43 @@ def lpb_scaling_noalloc(m: int, n: int, nnz: int, row_ptr_dev: int, col_idx_dev:
     addresses (e.g. torch ``data_ptr()``); ``stream`` a cudaStream_t or None."""
     _check(load().lpb_scaling_noalloc(int(m), int(n), int(nnz), row_ptr_dev, col_idx_dev, vals_dev,
                                       int(ruiz_iters), int(pock_chambolle), d_row_dev, d_col_dev, stream))
+
+
+def lpb_obbt_tighten(b, specs: np.ndarray, var_lo, var_hi, min_gain: float = 1e-4):
+    """New variable bounds from a solved OBBT batch: (new_lo, new_hi, updated)."""
+    sp = np.ascontiguousarray(specs, dtype=SPEC_DTYPE)
+    lo = np.ascontiguousarray(var_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(var_hi, dtype=np.float64)
+    nlo, nhi = np.empty_like(lo), np.empty_like(hi)
+    cnt = C.c_int32()
+    _check(load().lpb_obbt_tighten(b, _ptr(sp) if sp.size else None, _ptr(lo), _ptr(hi), float(min_gain), _ptr(nlo),
+                                   _ptr(nhi), C.byref(cnt)))
+    return nlo, nhi, cnt.value
+
+
+def lpb_get_tuning(h) -> Tuning:
+    t = Tuning()
+    _check(load().lpb_get_tuning(h, C.byref(t)))
+    return t
+
+
+def lpb_set_tuning(h, t: Tuning) -> None:
+    _check(load().lpb_set_tuning(h, C.byref(t)))
+
+
+def lpb_autotune(h, num_lps: int) -> Tuning:
+    t = Tuning()
+    _check(load().lpb_autotune(h, int(num_lps), C.byref(t)))
+    return t
+
+
+def lpb_tune_batch(h, widths):
+    """(microseconds per iteration for each width, index of the best width)"""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    us = np.zeros(w.size)
+    best = C.c_int32()
+    _check(load().lpb_tune_batch(h, _ptr(w), int(w.size), _ptr(us), C.byref(best)))
+    return us, best.value
 
 
 def lpb_batch_free(b) -> None:
@@ -431,6 +483,18 @@ class Handle:
 
     def info(self):
         return lpb_handle_info(self.ptr)
+
+    def tuning(self) -> Tuning:
+        return lpb_get_tuning(self.ptr)
+
+    def set_tuning(self, t: Tuning) -> None:
+        lpb_set_tuning(self.ptr, t)
+
+    def autotune(self, num_lps: int) -> Tuning:
+        return lpb_autotune(self.ptr, num_lps)
+
+    def tune_batch(self, widths):
+        return lpb_tune_batch(self.ptr, widths)
 
     def scaling(self):
         return lpb_scaling(self.ptr, self.m, self.n)

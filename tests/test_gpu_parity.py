@@ -493,3 +493,95 @@ def test_obbt_polish_tight_tolerance(lpb, orc, arith):
         r, x, y = b.result(q)
         k = orc.kkt_spec(w.lp, w.specs, q, x, y)
         assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-6, (q, k)
+
+
+# ---------------------------------------------------------------------------
+# OBBT safe bounds (Sec. 6 "OBBT results")
+# ---------------------------------------------------------------------------
+
+def highs_optimum(lp, specs, q):
+    from scipy.optimize import linprog
+    from scipy.sparse import vstack
+
+    c, xl, xu = _child(lp, specs, q)
+    a = _csr(lp)
+    fu, fl = np.isfinite(lp.row_hi), np.isfinite(lp.row_lo)
+    aub = vstack([a[fu], -a[fl]]).tocsr()
+    bub = np.concatenate([lp.row_hi[fu], -lp.row_lo[fl]])
+    bounds = [(None if np.isinf(v) else v, None if np.isinf(w) else w) for v, w in zip(xl, xu)]
+    r = linprog(c, A_ub=aub, b_ub=bub, bounds=bounds, method="highs")
+    return r.status, (r.fun if r.status == 0 else None)
+
+
+def test_obbt_safe_bounds_hold(lpb, orc):
+    """With the paper's OBBT settings (eps_dual = 1e-8, the Delta shift, the
+    1e-4 update rule) every tightened bound contains HiGHS's exact range of
+    the variable, and the dual residual of each optimal LP meets 1e-8 in the
+    oracle's own evaluation."""
+    w = lpgen.obbt_square(seed=1, m=1500, n=1500, lps=32)
+    lp = w.lp
+    h = lpb.Handle(lp, precision=lpb.MIXED, eps_dual=1e-8)
+    b = h.solve(w.specs, tol=1e-6, max_iter=400000)
+    res = b.results()
+    assert np.mean(res["status"] == 0) >= 0.9, np.bincount(res["status"])
+    for q in np.nonzero(res["status"] == 0)[0][:8]:
+        r, x, y = b.result(int(q))
+        k = orc.kkt_spec(lp, w.specs, int(q), x, y)
+        assert k["rel_dual"] <= 2e-8, (q, k)
+    sp = lpb.specs_from(w.specs)
+    new_lo, new_hi, cnt = lpb.lpb_obbt_tighten(b.ptr, sp, lp.var_lo, lp.var_hi, 1e-4)
+    assert cnt >= 1
+    changed = 0
+    for q in range(len(w.specs)):
+        st, fun = highs_optimum(lp, w.specs, q)
+        j = int(w.specs.var[q])
+        if res["status"][q] == 0:
+            assert st == 0
+            # the certified bound never cuts off the true optimum
+            assert res["safe_bound"][q] <= fun + 1e-9 * (1 + abs(fun)), (q, res["safe_bound"][q], fun)
+        if w.specs.sign[q] > 0 and st == 0:
+            assert new_lo[j] <= fun + 1e-9 * (1 + abs(fun)), (q, new_lo[j], fun)
+        if w.specs.sign[q] < 0 and st == 0:
+            assert new_hi[j] >= -fun - 1e-9 * (1 + abs(fun)), (q, new_hi[j], -fun)
+    changed = int(np.sum(new_lo != lp.var_lo) + np.sum(new_hi != lp.var_hi))
+    assert changed == cnt
+    # the update rule: a bound moves only by more than 1e-4
+    moved = np.concatenate([(new_lo - lp.var_lo)[new_lo != lp.var_lo], (lp.var_hi - new_hi)[new_hi != lp.var_hi]])
+    assert np.all(moved > 1e-4)
+
+
+def test_graphs_and_pdl_leave_results_unchanged(lpb):
+    """The interval as a replayed CUDA graph with programmatically dependent
+    step kernels computes exactly what plain launches compute."""
+    w = lpgen.sb_powerlaw(seed=1, m=4000, n=9000, children=24)
+    ref = lpb.Handle(w.lp, precision=lpb.MIXED, use_graphs=0, use_pdl=0).solve(w.specs, tol=1e-5).results()
+    for g, p in ((1, 0), (0, 1), (1, 1)):
+        res = lpb.Handle(w.lp, precision=lpb.MIXED, use_graphs=g, use_pdl=p).solve(w.specs, tol=1e-5).results()
+        for f in ("status", "iters", "restarts", "obj", "rel_primal", "rel_dual", "rel_gap"):
+            np.testing.assert_array_equal(res[f], ref[f], err_msg=f"{f} graphs={g} pdl={p}")
+
+
+def test_autotune_and_batch_size_by_timing(lpb, orc):
+    """The autotuner picks valid launch shapes; a solve with them keeps the
+    oracle's results; the batch-size timing reports every width."""
+    w = lpgen.sb_powerlaw(seed=0)
+    ref = golden_ref("sb_powerlaw_seed0")
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    t0 = h.tuning()
+    assert (t0.long_row_primal, t0.long_row_dual, t0.lane_shift_primal, t0.lane_shift_dual) == (32, 32, 0, 0)
+    t = h.autotune(len(w.specs))
+    assert t.long_row_primal in (8, 16, 32, 64, 128, 256) and t.long_row_dual in (8, 16, 32, 64, 128, 256)
+    assert 0 <= t.lane_shift_primal <= 2 and 0 <= t.lane_shift_dual <= 2
+    got = h.tuning()
+    assert (got.long_row_primal, got.long_row_dual) == (t.long_row_primal, t.long_row_dual)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    assert_parity(orc, w.lp, w.specs, b, ref, kkt_lps=range(0, 64, 9))
+    # every shape gives a correct solve (long rows on several block shapes)
+    for shape in ((8, 256, 1, 2), (256, 8, 2, 0)):
+        h.set_tuning(lpb.Tuning(*shape))
+        b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+        assert_parity(orc, w.lp, w.specs, b, ref, kkt_lps=[0, 40])
+    with pytest.raises(lpb.LpbError):
+        h.set_tuning(lpb.Tuning(0, 32, 0, 0))
+    us, best = h.tune_batch([1, 8, 64, 256])
+    assert us.shape == (4,) and np.all(us > 0) and 0 <= best < 4
