@@ -366,6 +366,10 @@ def main():
     ap.add_argument("--cpu-lps", type=int, default=64, help="oracle sample size for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--b1-lps", type=int, default=8, help="LPs solved one at a time for the B=1 comparison")
+    ap.add_argument("--lps", type=int, default=0, help="solve only the first N LPs of the workload (0: all)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed solves and one profiled repeat: no B=1 loop, cuSPARSE comparison, width "
+                         "sweep or end-to-end leg (the form the ncu captures run)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -395,6 +399,8 @@ def main():
 
     # each rank: its own seeded batch (weak scaling)
     w = WORKLOADS[args.workload]["fn"](args.seed + rank)
+    if args.lps > 0 and args.lps < len(w.specs):
+        w = lpgen.Workload(w.lp, w.specs.subset(range(args.lps)), w.precision, f"{w.name} (first {args.lps} LPs)")
     max_iter = WORKLOADS[args.workload]["max_iter"]
     precision = lpb.FP64 if w.precision == "fp64" else lpb.MIXED
     # timed solves: CUDA graphs and programmatic dependent launch, no per-launch events
@@ -440,7 +446,7 @@ def main():
     # every launch (plain launches; graphs and PDL need no events between kernels)
     hp = lpb.Handle(w.lp, options=lpb.lpb_default_options(precision=precision, profile=1, device=local,
                                                          cuda_stream=stream.cuda_stream))
-    prof_steps = max(1, min(args.steps, 3))
+    prof_steps = 1 if args.no_extras else max(1, min(args.steps, 3))
     profs = []
     for _ in range(prof_steps):
         flush.zero_()
@@ -471,18 +477,20 @@ def main():
 
     # the paper's engine on the same shape, and the step time against the batch
     # width (the synthetic analogue of the paper's SpMM-vs-N figure)
-    try:
-        cus = cusparse_spmm(w.lp, q, dev)
-    except Exception as ex:  # torch without CSR SpMM support on this device
-        cus = {"unavailable": str(ex)[:120]}
-    widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
-    us_w, best_w = h.tune_batch(widths)
-    width_sweep = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
-                   "best_width": widths[best_w],
-                   "what": "one iteration (primal + dual step) on N copies of the base LP, plain launches"}
+    cus, width_sweep = None, None
+    if not args.no_extras:
+        try:
+            cus = cusparse_spmm(w.lp, q, dev)
+        except Exception as ex:  # torch without CSR SpMM support on this device
+            cus = {"unavailable": str(ex)[:120]}
+        widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+        us_w, best_w = h.tune_batch(widths)
+        width_sweep = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
+                       "best_width": widths[best_w],
+                       "what": "one iteration (primal + dual step) on N copies of the base LP, plain launches"}
 
     # B=1 loop: the same kernels, one LP per solve
-    b1_n = min(args.b1_lps, q)
+    b1_n = 0 if args.no_extras else min(args.b1_lps, q)
     b1_specs = [torch.from_numpy(specs_np[i:i + 1].view(np.uint8).copy()).to(dev) for i in range(b1_n)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -500,7 +508,7 @@ def main():
     lp = w.lp
     h2d = (lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.vals.nbytes + lp.c.nbytes + lp.row_lo.nbytes +
            lp.row_hi.nbytes + lp.var_lo.nbytes + lp.var_hi.nbytes + specs_np.nbytes)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_extras else max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_solved, d2h = 0, 0
@@ -513,7 +521,7 @@ def main():
         be.free()
         he.close()
     e2e_s = time.perf_counter() - t0
-    e2e_value = e2e_solved / e2e_s * (world if dist else 1)
+    e2e_value = e2e_solved / e2e_s * (world if dist else 1) if e2e_steps else None
 
     out = None
     if rank == 0:

@@ -91,6 +91,8 @@ void set_result(lpb_lp_result& r, const ColRecord& rc, int status, int64_t iters
 template <typename T>
 lpb_err compact(lpb_ctx* h, Lane& ln, const std::vector<int>& gone, cudaStream_t s, lpb_profile* prof) {
     if (gone.empty()) return LPB_OK;
+    // the pinned move lists may still be read by copies queued earlier
+    LPB_CU(cudaStreamSynchronize(s));
     const int ncol = ln.ncol;
     std::vector<char> is_gone(ncol, 0);
     for (int f : gone) is_gone[f] = 1;
@@ -490,6 +492,7 @@ lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaS
     }
     if (fin.empty()) return LPB_OK;
     const int cnt = (int)fin.size();
+    LPB_CU(cudaStreamSynchronize(s));  // pinned lists free for reuse
     int* cols = ln.mv_h + 2 * ln.cap;
     for (int f = 0; f < cnt; ++f) {
         const int j = fin[f];
@@ -530,6 +533,7 @@ lpb_err lane_migrate(lpb_ctx* h, Lane& src, Lane& dst, GroupRun& g, int id_dst, 
     const int cnt = (int)sc.size();
     if (dst.ncol + cnt > dst.cap) return fail(LPB_ERR_INVALID_ARG, "polish lane has too few free columns");
     if (id_dst < 0 || id_dst >= dst.gcap) return fail(LPB_ERR_INVALID_ARG, "bad polish group id");
+    LPB_CU(cudaStreamSynchronize(s));  // pinned lists free for reuse
     LPB_CU(cudaMemcpyAsync(dst.ctl + id_dst, src.ctl + g.id, sizeof(Control), cudaMemcpyDeviceToDevice, s));
     const CheckData dcd = lane_check_data(h, dst, 0);
     LPB_CU(launch_group_moved(dcd, id_dst, slot0_dst, s));

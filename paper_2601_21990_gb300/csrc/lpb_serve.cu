@@ -461,9 +461,14 @@ lpb_err lpb_server_attach(lpb_server_t srv, lpb_handle h, int32_t* matrix_id) {
     lpb_err rc = lane_reserve(h, M->lane32, kPrecF32, srv->opt.lane_columns, srv->opt.max_groups);
     if (rc == LPB_OK && pcols > 0) rc = lane_reserve(h, M->lanep, M->polish_prec, pcols, srv->opt.max_groups);
     if (rc == LPB_OK) rc = ensure_check_ws(h, std::max(M->lane32.cap, M->lanep.cap));
-    if (rc == LPB_OK && h->opt.profile) {
-        // per-interval event timing is not collected by the server
+    if (rc == LPB_OK) {
+        // the server launches intervals plainly: its lanes change shape at
+        // almost every interval (admissions, completions, moves), so a
+        // captured graph would rarely be replayed; per-interval event timing
+        // is not collected
         h->opt.profile = 0;
+        h->opt.use_graphs = 0;
+        h->opt.use_pdl = 0;
     }
     std::lock_guard<std::mutex> lk(srv->mu);
     if (rc != LPB_OK) {

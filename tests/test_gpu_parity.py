@@ -546,7 +546,8 @@ def test_obbt_safe_bounds_hold(lpb, orc):
     changed = int(np.sum(new_lo != lp.var_lo) + np.sum(new_hi != lp.var_hi))
     assert changed == cnt
     # the update rule: a bound moves only by more than 1e-4
-    moved = np.concatenate([(new_lo - lp.var_lo)[new_lo != lp.var_lo], (lp.var_hi - new_hi)[new_hi != lp.var_hi]])
+    lo_m, hi_m = new_lo != lp.var_lo, new_hi != lp.var_hi
+    moved = np.concatenate([new_lo[lo_m] - lp.var_lo[lo_m], lp.var_hi[hi_m] - new_hi[hi_m]])
     assert np.all(moved > 1e-4)
 
 
