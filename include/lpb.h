@@ -238,7 +238,7 @@ lpb_err lpb_get_tuning(lpb_handle h, lpb_tuning* t);
 lpb_err lpb_set_tuning(lpb_handle h, const lpb_tuning* t);
 
 /* Autotuner: times the primal and dual steps on num_lps copies of the base
- * LP for every threshold in {8, 16, 32, 64, 128, 256} and shift in {0, 1, 2},
+ * LP for every threshold in {8, 16, 32, 64, 128, 256} and shift in {0, ..., 4},
  * applies the fastest shape of each step to the handle and returns it in
  * *chosen (may be NULL).  Takes a few hundred step launches. */
 lpb_err lpb_autotune(lpb_handle h, int32_t num_lps, lpb_tuning* chosen);

@@ -663,7 +663,7 @@ lpb_err lpb_autotune(lpb_handle h, int32_t num_lps, lpb_tuning* chosen) {
     int bp_thr = h->At.long_thr, bp_sh = h->At.g_shift, bd_thr = h->A.long_thr, bd_sh = h->A.g_shift;
     lpb_err rc;
     for (int thr : thrs) {
-        for (int sh = 0; sh <= 2; ++sh) {
+        for (int sh = 0; sh <= 4; ++sh) {
             // both steps take the candidate; each step keeps its own best
             if ((rc = apply_shape(h, h->At, thr, sh)) != LPB_OK) return rc;
             if ((rc = apply_shape(h, h->A, thr, sh)) != LPB_OK) return rc;
