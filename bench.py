@@ -52,6 +52,26 @@ def dist_env():
     return rank, world, local
 
 
+def rank_workload(name: str, seed: int, rank: int):
+    """Weak scaling over replicas: rank r solves its own batch, seeded seed + r,
+    so ranks share no data and need no collective on the data path."""
+    return WORKLOADS[name]["fn"](seed + rank)
+
+
+def reduce_over_ranks(dist, elapsed, solved, device):
+    """Whole-job figures over the replicas: the slowest rank's time (max) and
+    the LPs solved by all ranks (sum).  dist is torch.distributed or None."""
+    if dist is None:
+        return float(elapsed), int(solved)
+    import torch
+
+    t = torch.tensor([float(elapsed)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(solved)], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), int(round(c.item()))
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -117,20 +137,20 @@ class ClockSampler:
 
 
 def ncu_traffic(kernel_name: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    """DRAM bytes per launch from a committed ncu summary and how they were
+    taken, if they were taken on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except Exception:
-        return None
+        return None, None
     src = os.path.join(ROOT, "paper_2601_21990_gb300", "csrc", "lpb_iter.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = d.get(workload, {}).get(kernel_name)
     if not ent or ent.get("lpb_iter_sha") != h:
-        return None
-    return ent.get("dram_bytes_per_launch")
+        return None, None
+    return ent.get("dram_bytes_per_launch"), f"ncu DRAM bytes of one {ent.get('ncol')}-LP launch: {ent.get('note')}"
 
 
 def run_reference(args, rank, world):
@@ -279,15 +299,7 @@ def run_serving(args, rank, world, local):
                                           info.polished))
         srv.release(r)
     total_s = wall
-    if dist:
-        t = torch.tensor([wall], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        c = torch.tensor([nsolved], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(c)
-        nsolved_all = int(c.item())
-    else:
-        nsolved_all = nsolved
+    total_s, nsolved_all = reduce_over_ranks(dist, wall, nsolved, f"cuda:{local}")
     value = nsolved_all / total_s
     if rank == 0:
         print(json.dumps({
@@ -398,7 +410,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     # each rank: its own seeded batch (weak scaling)
-    w = WORKLOADS[args.workload]["fn"](args.seed + rank)
+    w = rank_workload(args.workload, args.seed, rank)
     if args.lps > 0 and args.lps < len(w.specs):
         w = lpgen.Workload(w.lp, w.specs.subset(range(args.lps)), w.precision, f"{w.name} (first {args.lps} LPs)")
     max_iter = WORKLOADS[args.workload]["max_iter"]
@@ -454,15 +466,7 @@ def main():
         profs.append(b.profile())
         b.free()
     hp.close()
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        cnt = torch.tensor([nsolved], device=dev, dtype=torch.float64)
-        dist.all_reduce(cnt)
-        nsolved_all = int(cnt.item())
-    else:
-        nsolved_all = nsolved
+    total_ms, nsolved_all = reduce_over_ranks(dist, total_ms, nsolved, dev)
     value = nsolved_all / (total_ms / 1e3)
 
     # roofline of the dominant kernel, from the library's CUDA events on this stream
@@ -473,7 +477,7 @@ def main():
     dom = int(np.argmax(ms[:2]))
     achieved = by[dom] / (ms[dom] / 1e3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = ncu_traffic(["k_primal", "k_dual"][dom], args.workload)
+    traffic, traffic_note = ncu_traffic(["k_primal", "k_dual"][dom], args.workload)
 
     # the paper's engine on the same shape, and the step time against the batch
     # width (the synthetic analogue of the paper's SpMM-vs-N figure)
@@ -483,7 +487,11 @@ def main():
             cus = cusparse_spmm(w.lp, q, dev)
         except Exception as ex:  # torch without CSR SpMM support on this device
             cus = {"unavailable": str(ex)[:120]}
-        widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+        # widths whose lane and check workspace fit in half the free memory
+        # (about 44 n + 36 m bytes per FP32 column)
+        per_col = 44.0 * w.lp.n + 36.0 * w.lp.m
+        free_b = torch.cuda.mem_get_info(dev)[0]
+        widths = [k for k in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096) if k * per_col < 0.5 * free_b]
         us_w, best_w = h.tune_batch(widths)
         width_sweep = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
                        "best_width": widths[best_w],
@@ -539,7 +547,7 @@ def main():
                        "lps_solved_per_step": nsolved / args.steps},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": traffic, "launches": int(la[dom]),
+                         "traffic": traffic, "traffic_note": traffic_note, "launches": int(la[dom]),
                          "avg_launch_us": 1e3 * ms[dom] / max(la[dom], 1),
                          "timing": f"CUDA events around every launch over {prof_steps} profiled repeats of the "
                                    "timed solve (plain launches)",
