@@ -27,7 +27,10 @@ namespace lpb {
 constexpr int kBlock = LPB_BLOCK;     // threads of every iteration / SpMM block
 constexpr int kLongRow = LPB_LONG_ROW; // rows with more nonzeros get a whole block
 constexpr int kReduceRows = 8;     // rows per step of a reduction block (blockDim.y)
-constexpr int kReduceBlocks = 304; // reduction blocks per column tile (2 per SM)
+#ifndef LPB_REDUCE_BLOCKS
+#define LPB_REDUCE_BLOCKS 304
+#endif
+constexpr int kReduceBlocks = LPB_REDUCE_BLOCKS; // reduction blocks per column tile (fixed: the sum order)
 constexpr int kNumStats = 18;      // per-column partial sums of a check
 
 // per-column statistics produced by a check (indices into the stats arrays)
