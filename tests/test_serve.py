@@ -232,3 +232,31 @@ def test_bad_requests_are_rejected(lpb):
     srv.wait(r, 60)
     assert srv.results(r)["status"][0] == 0
     srv.close()
+
+
+def test_polish_moves_beside_running_requests(lpb, orc):
+    """A request that stalls moves to the polish lane while other requests
+    keep running (and finish, and compact) in the FP32 lane of the same
+    matrix: every request finishes with results the oracle accepts."""
+    w = lpgen.sb_small(seed=3)
+    h = lpb.Handle(w.lp, precision=lpb.MIXED, polish_stall_checks=4)
+    srv = lpb.Server(lane_columns=96, polish_columns=32)
+    mid = srv.attach(h)
+    rng = np.random.default_rng(11)
+    tight = srv.submit(mid, w.specs, tol=1e-7, max_iter=400000)
+    loose = [srv.submit(mid, lpgen.sb_specs(w.lp.x0, rng.choice(w.lp.n, size=k, replace=False)), tol=TOL,
+                        max_iter=400000) for k in (6, 9, 12, 7)]
+    for r in [tight] + loose:
+        srv.wait(r, 300)
+    assert srv.info(tight).polished == 1
+    for r, tol in [(tight, 1e-6)] + [(q, TOL) for q in loose]:
+        res = srv.results(r)
+        sp = w.specs if r == tight else None
+        assert np.all(res["status"] <= 3)
+        if sp is not None:
+            for q in np.nonzero(res["status"] == 0)[0][:6]:
+                rr, x, y = srv.result(r, mid, int(q))
+                k = orc.kkt_spec(w.lp, sp, int(q), x, y)
+                assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= tol, (q, k)
+    assert srv.stats().migrations >= 1
+    srv.close()
