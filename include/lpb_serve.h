@@ -1,8 +1,8 @@
 /* lpb_serve.h -- continuous batching of LP solve requests on one GPU.
  *
- * A server owns a worker thread that keeps the active LPs of every attached
- * handle (one sparse A each, lpb.h) on the device and advances them interval
- * by interval: check_every iterations of the batched restarted Halpern PDHG
+ * A server keeps the active LPs of every attached handle (one sparse A each,
+ * lpb.h) on the device; one worker thread per attached handle advances them
+ * interval by interval: check_every iterations of the batched restarted Halpern PDHG
  * (Sec. 4-5 of the paper) followed by the FP64-accurate check.  Each request
  * -- a set of strong-branching children (Sec. 5.1) or bound-tightening LPs
  * (Sec. 5.2) of one matrix -- becomes one restart group: its LPs share the
@@ -71,7 +71,7 @@ typedef struct {
     int64_t column_iters;      /* sum over intervals of active columns x iterations */
     int64_t admitted_while_busy;  /* requests admitted into a lane that had other work */
     int64_t migrations;        /* requests moved to a polish lane */
-    double busy_s;             /* worker time with device work in flight */
+    double busy_s;             /* time during which some matrix had device work in flight */
     int64_t hbm_used_bytes, hbm_budget_bytes;
     int64_t kernels;           /* kernel launches of the intervals and checks */
 } lpb_server_stats;

@@ -1,7 +1,7 @@
-// lpb_serve.cu -- the serving loop of include/lpb_serve.h: a worker thread
-// that admits requests into the lanes of their matrices between intervals
-// (continuous batching), runs one interval on every lane with work (the
-// lanes of different matrices on their own streams, so they overlap on the
+// lpb_serve.cu -- the serving loop of include/lpb_serve.h: one worker thread
+// per attached matrix admits requests into the matrix's lanes between
+// intervals (continuous batching), runs one interval on each of its lanes
+// with work (on the matrix's own stream, so the matrices overlap on the
 // device), collects finished LPs and moves stalled requests to the polish
 // lane.  Every step of the method runs in the kernels; this file schedules.
 #include <algorithm>
@@ -70,7 +70,9 @@ struct lpb_server {
     lpb_server_options opt{};
     int device = 0;
     Clock::time_point t0;
-    std::thread worker;
+    std::vector<std::thread> workers;  // one per attached matrix
+    int in_flight = 0;                  // matrices with device work queued
+    Clock::time_point busy_since;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
@@ -313,41 +315,47 @@ lpb_err finish(lpb_server* srv, Matrix& M, lpb_server_stats& add, lpb_profile& p
     return LPB_OK;
 }
 
-// One pass of the worker.  Each matrix advances on its own stream: one whose
-// interval has completed is collected, takes in admissions and launches its
-// next interval at once, without waiting for the other matrices.
-lpb_err step(lpb_server* srv, bool& did_work, bool& in_flight) {
+// device-busy time: some matrix has an interval in flight
+void mark_in_flight(lpb_server* srv, int delta) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const int before = srv->in_flight;
+    srv->in_flight += delta;
+    if (before == 0 && srv->in_flight > 0) srv->busy_since = Clock::now();
+    if (before > 0 && srv->in_flight == 0)
+        srv->st.busy_s += std::chrono::duration<double>(Clock::now() - srv->busy_since).count();
+}
+
+// One pass of matrix M's worker: once its interval has completed it is
+// collected, takes in admissions and launches its next interval at once.
+lpb_err step_matrix(lpb_server* srv, Matrix& M, int mi, bool& did_work) {
     did_work = false;
-    in_flight = false;
-    std::vector<Matrix*> mats;
-    std::vector<std::pair<int, void*>> frees;
+    std::vector<void*> frees;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        for (auto& mp : srv->mats) mats.push_back(mp.get());
-        frees.swap(srv->to_free);
+        std::vector<std::pair<int, void*>> keep;
+        for (const auto& f : srv->to_free) {
+            if (f.first == mi) frees.push_back(f.second);
+            else keep.push_back(f);
+        }
+        srv->to_free.swap(keep);
     }
-    for (const auto& f : frees) LPB_CU(cudaFreeAsync(f.second, mats[f.first]->h->stream));
+    for (void* p : frees) LPB_CU(cudaFreeAsync(p, M.h->stream));
     lpb_server_stats add{};
     lpb_profile prof{};
     lpb_err rc;
-    for (Matrix* mp : mats) {
-        Matrix& M = *mp;
-        if (M.in_flight) {
-            const cudaError_t q = cudaStreamQuery(M.h->stream);
-            if (q == cudaErrorNotReady) {
-                in_flight = true;
-                continue;
-            }
-            if (q != cudaSuccess) return cuda_fail(q, "cudaStreamQuery");
-            if ((rc = finish(srv, M, add, prof)) != LPB_OK) return rc;
-            did_work = true;
-        }
-        if ((rc = admit_pending(srv, M, did_work)) != LPB_OK) return rc;
-        if ((rc = launch(srv, M, add, prof)) != LPB_OK) return rc;
-        if (M.in_flight) {
-            in_flight = true;
-            did_work = true;
-        }
+    if (M.in_flight) {
+        const cudaError_t q = cudaStreamQuery(M.h->stream);
+        if (q == cudaErrorNotReady) return LPB_OK;
+        if (q != cudaSuccess) return cuda_fail(q, "cudaStreamQuery");
+        mark_in_flight(srv, -1);
+        if ((rc = finish(srv, M, add, prof)) != LPB_OK) return rc;
+        did_work = true;
+    }
+    if ((rc = admit_pending(srv, M, did_work)) != LPB_OK) return rc;
+    if ((rc = launch(srv, M, add, prof)) != LPB_OK) return rc;
+    if (M.in_flight) {
+        mark_in_flight(srv, +1);
+        did_work = true;
     }
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->st.intervals += add.intervals;
@@ -357,34 +365,32 @@ lpb_err step(lpb_server* srv, bool& did_work, bool& in_flight) {
     return LPB_OK;
 }
 
-void worker_main(lpb_server* srv) {
+// The worker of one attached matrix.  Matrices advance independently: each
+// has its own thread, stream and lanes, so a small matrix's short intervals
+// are not held back by the host work (collection, admission, launches) of
+// the others.
+void worker_main(lpb_server* srv, Matrix* M, int mi) {
     cudaSetDevice(srv->device);
-    auto busy_since = Clock::now();
-    bool was_busy = false;
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(srv->mu);
-            if (srv->stop) return;
+            if (srv->stop || srv->fatal_code != LPB_OK) return;
         }
-        bool did = false, in_flight = false;
-        lpb_err rc = step(srv, did, in_flight);
-        const auto t = Clock::now();
-        if (in_flight && !was_busy) busy_since = t;
-        if (!in_flight && was_busy) {
-            std::lock_guard<std::mutex> lk(srv->mu);
-            srv->st.busy_s += std::chrono::duration<double>(t - busy_since).count();
-        }
-        was_busy = in_flight;
+        bool did = false;
+        lpb_err rc = step_matrix(srv, *M, mi, did);
         if (rc != LPB_OK) {
             std::lock_guard<std::mutex> lk(srv->mu);
-            srv->fatal_code = rc;
-            srv->fatal_msg = lpb_last_error();
+            if (srv->fatal_code == LPB_OK) {
+                srv->fatal_code = rc;
+                srv->fatal_msg = lpb_last_error();
+            }
             for (auto& kv : srv->reqs)
                 if (kv.second->state == kPending || kv.second->state == kRunning) kv.second->state = kFailed;
             srv->cv_done.notify_all();
+            srv->cv_work.notify_all();
             return;
         }
-        if (in_flight) {
+        if (M->in_flight) {
             // device work outstanding: poll again shortly
             if (!did) std::this_thread::sleep_for(std::chrono::microseconds(20));
         } else if (!did) {
@@ -436,7 +442,6 @@ lpb_err lpb_server_create(const lpb_server_options* opt, lpb_server_t* out) {
     }
     srv->budget = budget;
     srv->st.hbm_budget_bytes = budget;
-    srv->worker = std::thread(worker_main, srv);
     *out = srv;
     return LPB_OK;
 }
@@ -478,8 +483,10 @@ lpb_err lpb_server_attach(lpb_server_t srv, lpb_handle h, int32_t* matrix_id) {
         return rc;
     }
     *matrix_id = (int32_t)srv->mats.size();
+    Matrix* mp = M.get();
     srv->mats.push_back(std::move(M));
     srv->st.hbm_used_bytes = srv->used;
+    srv->workers.emplace_back(worker_main, srv, mp, (int)*matrix_id);
     return LPB_OK;
 }
 
@@ -662,7 +669,8 @@ void lpb_server_destroy(lpb_server_t srv) {
         srv->stop = true;
         srv->cv_work.notify_all();
     }
-    if (srv->worker.joinable()) srv->worker.join();
+    for (auto& w : srv->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(srv->device);
     for (auto& mp : srv->mats) {
         if (mp->h && mp->h->stream) cudaStreamSynchronize(mp->h->stream);
