@@ -958,6 +958,73 @@ __global__ void k_reduce_n_df(const ReduceDfArgs<TI> a) {
     write_partials<10>(s, a.part, S_DRES2, kReduceBlocks, a.ld, j, ok);
 }
 
+// The n-side check in one pass, for a transpose without long rows: thread
+// (x, y) of a block takes column j of its 32-column tile and rows y, y + 8,
+// ... of the block's row set (the same rows and order as k_reduce_n_df);
+// for each row it forms c + A^T y^, A^T Pi_B(dy) and A^T dy from the row's
+// entries in double-float (the warp shares the row's entries, each thread
+// gathers its column) and folds them straight into the per-column
+// statistics, so the three n x N products never go to memory.
+template <typename TI>
+__global__ void k_check_n_df(const ReduceDfArgs<TI> a, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const float* __restrict__ vhi, const float* __restrict__ vlo) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const bool ok = j < a.ncol;
+    const int jj = ok ? j : blockIdx.y * 32;  // lanes past the last LP read a valid column
+    float f_dres2 = 0.f, f_c2 = 0.f, f_dx2 = 0.f, f_dx02 = 0.f, f_res2 = 0.f, f_rx2 = 0.f;
+    df d_ctx = df_zero(), d_phr = df_zero(), d_phidr = df_zero(), d_cdx = df_zero();
+    const int kind = a.col.kind[jj], var = a.col.var[jj];
+    const df olo = df_from(a.col.lo[jj]), ohi = df_from(a.col.hi[jj]), oc = df_from(a.col.c[jj]);
+    for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.n; i += gridDim.x * kReduceRows) {
+        // A~^T [y^, Pi_B(dy), dy] for row i, column j
+        df q0 = df_zero(), q1 = df_zero(), q2 = df_zero();
+        const int end = rp[i + 1];
+        for (int e = rp[i]; e < end; ++e) {
+            const size_t src = (size_t)ci[e] * a.ld + jj;
+            const df w = df{vhi[e], vlo[e]};
+            df_fma_acc(q0, w, a.Yh[src]);
+            df_fma_acc(q1, w, a.DYp[src]);
+            df_fma_acc(q2, w, a.DY[src]);
+        }
+        q0 = quick_two_sum(q0.hi, q0.lo);
+        q1 = quick_two_sum(q1.hi, q1.lo);
+        q2 = quick_two_sum(q2.hi, q2.lo);
+        const size_t off = (size_t)i * a.ld + jj;
+        const df dc = a.dc[i], idc = a.idc[i];
+        df cj = a.c[i], lo = a.xl[i], hi = a.xu[i];
+        if (kind == 2) cj = var == i ? oc : df_zero();
+        else if (kind == 1 && var == i) { lo = olo; hi = ohi; }
+        const TI xh = a.Xh[off];
+        const df x = df_clamp(it_mul(dc, xh), lo, hi);
+        const df q = df_add(cj, df_mul(q0, idc));                    // c + A^T y
+        const df r = df_barrier(df_neg(q), lo, hi);                  // reduced cost
+        const float d = df_f(df_add(q, r));
+        f_dres2 += d * d;
+        f_c2 += cj.hi * cj.hi;
+        df_acc(d_ctx, df_mul(cj, x));
+        df_acc(d_phr, df_support(r, lo, hi));
+        const TI dx = a.DX[off];
+        const float dxs = it_f(dx);
+        f_dx2 += dxs * dxs;
+        const float dx0 = it_diff(a.restart_to_output ? xh : a.X[off], a.X0[off]);
+        f_dx02 += dx0 * dx0;
+        // A^T y^k = A^T y^ - A^T (y^ - y^k)
+        const df gk = df_mul(df_sub(q0, q2), idc);
+        const df rk = df_barrier(df_neg(df_add(cj, gk)), lo, hi);
+        const df drr = df_barrier(df_sub(r, rk), lo, hi);
+        df_acc(d_phidr, df_support(drr, lo, hi));
+        const float t = df_f(df_add(df_mul(q1, idc), drr));          // A^T dy + dr
+        f_res2 += t * t;
+        const df dxo = it_mul(dc, dx);
+        df_acc(d_cdx, df_mul(cj, dxo));
+        const float dxf = df_f(dxo);
+        const float t2 = dxf - proj_recession_f(dxf, lo.hi, hi.hi);
+        f_rx2 += t2 * t2;
+    }
+    double s[10] = {f_dres2, f_c2, df_d(d_ctx), df_d(d_phr), f_dx2, f_dx02, df_d(d_phidr), f_res2, df_d(d_cdx), f_rx2};
+    write_partials<10>(s, a.part, S_DRES2, kReduceBlocks, a.ld, j, ok);
+}
+
 }  // namespace
 
 template <typename T>
@@ -978,7 +1045,10 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     if constexpr (kDf) {
         if ((e = spmm_df<T, 2>(d.A, b.Xh, b.DX, nullptr, (df*)P0, (df*)P1, nullptr, ld, ncol, s)) != cudaSuccess)
             return e;
-        if ((e = spmm_df<T, 3>(d.At, b.Yh, b.DYp, b.DY, (df*)Q0, (df*)Q1, (df*)Q2, ld, ncol, s)) != cudaSuccess)
+        // without long rows in A~^T the n-side products are formed inside the
+        // n-side reduction (k_check_n_df)
+        if (d.At.n_long > 0 &&
+            (e = spmm_df<T, 3>(d.At, b.Yh, b.DYp, b.DY, (df*)Q0, (df*)Q1, (df*)Q2, ld, ncol, s)) != cudaSuccess)
             return e;
     } else {
         if ((e = spmm64<T, 2>(d.A, b.Xh, b.DX, nullptr, P0, P1, nullptr, ld, ncol, s)) != cudaSuccess) return e;
@@ -1058,7 +1128,10 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
             k_reduce_m_df<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(rd);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        k_reduce_n_df<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(rd);
+        if (d.At.n_long > 0)
+            k_reduce_n_df<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(rd);
+        else
+            k_check_n_df<T><<<dim3(nb_n, tiles), rblock, 0, s>>>(rd, d.At.rp, d.At.ci, d.At.v32, d.At.v32lo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         if (nb_m > 0) {
