@@ -586,3 +586,28 @@ def test_autotune_and_batch_size_by_timing(lpb, orc):
         h.set_tuning(lpb.Tuning(0, 32, 0, 0))
     us, best = h.tune_batch([1, 8, 64, 256])
     assert us.shape == (4,) and np.all(us > 0) and 0 <= best < 4
+
+
+def test_sb_large_full_size_properties(lpb, orc):
+    """m=1M, n=2M, nnz~10.5M (500 dense rows of 10k), B=128 as the bench runs
+    it: every LP ends optimal or certified infeasible, sampled LPs pass the
+    oracle's KKT evaluation, and no strong-branching child's optimum lies
+    below the parent LP's (Sec. 5.1: a child only shrinks the box)."""
+    w = lpgen.sb_large(seed=0)
+    h = lpb.Handle(w.lp, precision=lpb.MIXED)
+    b = h.solve(w.specs, tol=1e-4, max_iter=100000)
+    res = b.results()
+    assert np.all(res["status"] <= 2), np.bincount(res["status"])
+    for q in (0, 1, 63, 64, 127):
+        if res["status"][q] != 0:
+            continue
+        r, x, y = b.result(q)
+        k = orc.kkt_spec(w.lp, w.specs, q, x, y)
+        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-4, (q, k)
+    parent = h.solve(lpb.specs_array([0], [-1]), tol=1e-6, max_iter=100000).results()
+    assert parent["status"][0] == 0
+    f0 = parent["obj"][0]
+    opt = res["status"] == 0
+    # children at rel-gap 1e-4 may sit that far below their own optimum
+    slack = 2e-4 * (1.0 + np.abs(res["obj"][opt]) + abs(f0))
+    assert np.all(res["obj"][opt] >= f0 - slack), (res["obj"][opt].min(), f0)
