@@ -220,7 +220,12 @@ def run_serving(args, rank, world, local):
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     mats = lpgen.serving_matrices(seed0=args.seed + 10 * rank)
-    handles = [lpb.Handle(lp, precision=lpb.MIXED, device=local) for lp in mats]
+    # smaller matrices get more urgent streams: their short intervals take SMs
+    # ahead of the large matrices' queued kernels
+    order = np.argsort([lp.m for lp in mats])
+    prio = {int(k): -(len(mats) - 1 - r) if args.priorities else 0 for r, k in enumerate(order)}
+    handles = [lpb.Handle(lp, precision=lpb.MIXED, device=local, stream_priority=prio[k])
+               for k, lp in enumerate(mats)]
     srv = lpb.Server(lane_columns=512, polish_columns=64, max_groups=64, device=local)
     mids = [srv.attach(h) for h in handles]
     parents = [srv.submit(mid, lpb.specs_array([0], [-1]), tol=TOL, max_iter=100000) for mid in mids]
@@ -372,6 +377,7 @@ def main():
     ap.add_argument("--workload", default="sb_powerlaw", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--requests", type=int, default=160, help="serving: requests in the timed Poisson stream")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate as a fraction of capacity")
+    ap.add_argument("--priorities", type=int, default=1, help="serving: stream priorities by matrix size")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-lps", type=int, default=64)
     ap.add_argument("--ref-warmup", action="store_true")

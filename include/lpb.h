@@ -92,6 +92,11 @@ typedef struct {
                                        programmatic dependents, so each one's launch and parameter
                                        staging overlap the end of the previous one; not used when
                                        profile = 1 */
+    int32_t stream_priority;        /* priority of the stream lpb_create makes when cuda_stream is NULL
+                                       (CUDA's scale: lower is more urgent; clamped to the device's
+                                       range; default 0): on a shared GPU the blocks of more urgent
+                                       handles are scheduled first, e.g. small LPs served beside
+                                       large ones */
 } lpb_options;
 
 /* Values of lpb_options.polish_arith. */

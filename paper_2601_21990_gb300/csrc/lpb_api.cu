@@ -309,6 +309,7 @@ void lpb_default_options(lpb_options* o) {
     o->eps_dual = -1.0;
     o->use_graphs = 1;
     o->use_pdl = 1;
+    o->stream_priority = 0;
 }
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
@@ -377,7 +378,10 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
         if (o.cuda_stream) {
             h->stream = (cudaStream_t)o.cuda_stream;
         } else {
-            CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+            int lo = 0, hi = 0;  // least and greatest priority
+            CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            const int pr = std::max(hi, std::min(lo, (int)o.stream_priority));
+            CU(cudaStreamCreateWithPriority(&h->stream, cudaStreamNonBlocking, pr));
             h->own_stream = true;
         }
         cudaStream_t s = h->stream;

@@ -54,7 +54,7 @@ class Options(C.Structure):
                 ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32),
                 ("polish_arith", C.c_int32), ("eps_dual", C.c_double), ("use_graphs", C.c_int32),
-                ("use_pdl", C.c_int32)]
+                ("use_pdl", C.c_int32), ("stream_priority", C.c_int32)]
 
 
 class Spec(C.Structure):
