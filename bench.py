@@ -162,7 +162,8 @@ def run_reference(args, rank, world):
     oracle.build()
     w = WORKLOADS[args.workload]["fn"](args.seed)
     q = len(w.specs)
-    sample = min(q, args.ref_lps)
+    # a bounded sample per step: about 640 LP solves over the whole run
+    sample = min(q, args.ref_lps, max(4, 640 // max(args.steps, 1)))
     sp = w.specs.subset(range(sample))
     cores = os.cpu_count() or 1
     for _ in range(args.warmup if args.ref_warmup else 0):

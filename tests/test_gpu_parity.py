@@ -553,13 +553,15 @@ def test_obbt_safe_bounds_hold(lpb, orc):
 
 def test_graphs_and_pdl_leave_results_unchanged(lpb):
     """The interval as a replayed CUDA graph with programmatically dependent
-    step kernels computes exactly what plain launches compute."""
+    step kernels, on a stream of any priority, computes exactly what plain
+    launches compute."""
     w = lpgen.sb_powerlaw(seed=1, m=4000, n=9000, children=24)
     ref = lpb.Handle(w.lp, precision=lpb.MIXED, use_graphs=0, use_pdl=0).solve(w.specs, tol=1e-5).results()
-    for g, p in ((1, 0), (0, 1), (1, 1)):
-        res = lpb.Handle(w.lp, precision=lpb.MIXED, use_graphs=g, use_pdl=p).solve(w.specs, tol=1e-5).results()
+    for g, p, pr in ((1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, -1)):
+        res = lpb.Handle(w.lp, precision=lpb.MIXED, use_graphs=g, use_pdl=p, stream_priority=pr).solve(
+            w.specs, tol=1e-5).results()
         for f in ("status", "iters", "restarts", "obj", "rel_primal", "rel_dual", "rel_gap"):
-            np.testing.assert_array_equal(res[f], ref[f], err_msg=f"{f} graphs={g} pdl={p}")
+            np.testing.assert_array_equal(res[f], ref[f], err_msg=f"{f} graphs={g} pdl={p} priority={pr}")
 
 
 def test_autotune_and_batch_size_by_timing(lpb, orc):
