@@ -37,11 +37,12 @@ UNIT = "LPs/s"
 TOL = 1e-4
 FALLBACK_HBM_GBS = 6800.0
 
+# cpu_lps: the oracle's default sample (0: a single oracle solve takes minutes)
 WORKLOADS = {
-    "sb_powerlaw": dict(fn=lambda seed: lpgen.sb_powerlaw(seed=seed), max_iter=100000),
-    "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000),
-    "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000),
-    "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000),
+    "sb_powerlaw": dict(fn=lambda seed: lpgen.sb_powerlaw(seed=seed), max_iter=100000, cpu_lps=64),
+    "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000, cpu_lps=16),
+    "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000, cpu_lps=0),
+    "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000, cpu_lps=0),
 }
 
 
@@ -192,6 +193,9 @@ def run_reference(args, rank, world):
 def cpu_baseline(w, cores, budget_lps):
     import oracle
 
+    if budget_lps <= 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "none: one oracle solve of this workload takes minutes on the host cores"}
     oracle.build()
     q = len(w.specs)
     sample = min(q, budget_lps)
@@ -199,8 +203,16 @@ def cpu_baseline(w, cores, budget_lps):
     t = time.perf_counter()
     r = oracle.solve(w.lp, sp, tol=TOL, max_iter=100000, threads=cores, lockstep=0, want_xy=False)
     dt = time.perf_counter() - t
+    # the B=1 loop on one core, on a smaller sample
+    one = min(q, 2)
+    t = time.perf_counter()
+    r1 = oracle.solve(w.lp, w.specs.subset(range(one)), tol=TOL, max_iter=100000, threads=1, lockstep=0,
+                      want_xy=False)
+    dt1 = time.perf_counter() - t
     return {"value": int(np.sum(r.status <= 2)) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{sample} of {q} LPs of {w.name}, each alone, OpenMP over LPs, {dt:.1f} s"}
+            "sample": f"{sample} of {q} LPs of {w.name}, each alone, OpenMP over LPs, {dt:.1f} s",
+            "single_thread_b1": {"value": int(np.sum(r1.status <= 2)) / dt1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{one} LPs one after another on one core, {dt1:.1f} s"}}
 
 
 def run_serving(args, rank, world, local):
@@ -382,7 +394,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-lps", type=int, default=64)
     ap.add_argument("--ref-warmup", action="store_true")
-    ap.add_argument("--cpu-lps", type=int, default=64, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--cpu-lps", type=int, default=-1,
+                    help="oracle sample size for cpu_baseline (-1: the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--b1-lps", type=int, default=8, help="LPs solved one at a time for the B=1 comparison")
     ap.add_argument("--lps", type=int, default=0, help="solve only the first N LPs of the workload (0: all)")
@@ -541,7 +554,8 @@ def main():
     out = None
     if rank == 0:
         cores = os.cpu_count() or 1
-        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, cores, args.cpu_lps)
+        cpu_lps = args.cpu_lps if args.cpu_lps >= 0 else WORKLOADS[args.workload]["cpu_lps"]
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, cores, cpu_lps)
         setup_ms = profs[0].setup_ms if profs else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
