@@ -33,6 +33,11 @@
 #ifndef LPB_STEP_MIN_BLOCKS
 #define LPB_STEP_MIN_BLOCKS 5
 #endif
+// the same for the double-float instantiation, whose steps are bound by
+// instruction latency rather than DRAM: more resident warps hide more of it
+#ifndef LPB_STEP_MIN_BLOCKS_DF
+#define LPB_STEP_MIN_BLOCKS_DF 7
+#endif
 // gathers a lane issues before it consumes them (loads in flight per lane)
 #ifndef LPB_GATHER_BATCH
 #define LPB_GATHER_BATCH 4
@@ -46,6 +51,9 @@ template <typename T> struct Vec;
 template <> struct Vec<float> { static constexpr int V = 4; };
 template <> struct Vec<double> { static constexpr int V = 2; };
 template <> struct Vec<dfloat> { static constexpr int V = 2; };
+
+template <typename T> struct MinBlocks { static constexpr int v = LPB_STEP_MIN_BLOCKS; };
+template <> struct MinBlocks<dfloat> { static constexpr int v = LPB_STEP_MIN_BLOCKS_DF; };
 
 __device__ __forceinline__ void ldv(const float* p, float (&r)[4]) {
     float4 u = *reinterpret_cast<const float4*>(p);
@@ -319,7 +327,7 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
 //   taking rows g, g + stride, ...; while it gathers and finishes a row, the
 //   row pointers and the first index round of its next row are in flight.
 template <typename T, int G, bool CHECK, bool PRIMAL>
-__global__ void __launch_bounds__(kBlock, LPB_STEP_MIN_BLOCKS) k_step(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, MinBlocks<T>::v) k_step(const StepArgs<T> a) {
     constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
     constexpr int K = Round<T, G>::K, R = Round<T, G>::R;
     __shared__ T red[kBlock * V];
