@@ -97,10 +97,20 @@ typedef struct {
                                        range; default 0): on a shared GPU the blocks of more urgent
                                        handles are scheduled first, e.g. small LPs served beside
                                        large ones */
+    int32_t reduced_cost;           /* the reduced cost r of the stopping test (Sec. 4, Eq. stopping):
+                                       LPB_RC_BARRIER (default) r = Pi_B(-c - A^T y) as printed;
+                                       LPB_RC_ROBUST, the variant the paper's implementation uses
+                                       (PDLP's Appendix A): a component counts against a finite bound
+                                       only where the primal point lies no farther from that bound
+                                       than from zero, and otherwise stays in the dual residual, so
+                                       that large finite bounds do not swamp the dual objective and
+                                       the gap.  The infeasibility tests keep Pi_B in both modes */
 } lpb_options;
 
 /* Values of lpb_options.polish_arith. */
 enum { LPB_POLISH_DFLOAT = 0, LPB_POLISH_FP64 = 1 };
+/* Values of lpb_options.reduced_cost. */
+enum { LPB_RC_BARRIER = 0, LPB_RC_ROBUST = 1 };
 
 /* One override record (Sec. 5.1, 5.2). */
 typedef struct {
@@ -117,7 +127,7 @@ typedef struct {
     int32_t restarts;    /* batch restarts taken while this LP was active */
     int64_t iters;       /* PDHG iterations applied to this LP */
     double obj;          /* c^T x at the returned point */
-    double dual_obj;     /* -phi_[xlo,xhi](r) - phi_[l,u](y) (Sec. 3) */
+    double dual_obj;     /* -phi_[xlo,xhi](r) - phi_[l,u](y) (Sec. 3), r as lpb_options.reduced_cost */
     double rel_primal;   /* ||Ax - Pi_[l,u](Ax)|| / (1 + ||Ax||) */
     double rel_dual;     /* ||c + A^T y + r|| / (1 + ||c||) */
     double rel_gap;      /* |c^T x + phi + phi| / (1 + |c^T x| + |phi + phi|) */

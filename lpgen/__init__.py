@@ -295,6 +295,28 @@ def sb_large(seed: int = 0, m: int = 1000000, n: int = 2000000, dense_rows: int 
                     f"sb_large m={m} n={n} B={children} fp32-iterates/fp64-checks")
 
 
+def covering_large_bounds(seed: int = 0, m: int = 300, n: int = 500, big: float = 1e10) -> Workload:
+    """Covering LP whose variable boxes are mostly far larger than any
+    optimum reaches, the case the reduced cost robust to large bounds is for:
+    each column has U{3..5} distinct rows with values U[0.5, 3]; rows
+    A x >= b with b = U[0.3, 0.9] * (A x_f), x_f ~ U[0.5, 1] (so every LP
+    before branching is feasible); c ~ U[0.5, 2]; x in [0, big] for 80% of
+    the variables and [0, U[1, 3]] for the rest.  16 strong-branching
+    children = 8 random columns x {up, down} around x_rel ~ U[0.2, 2.8]."""
+    rng = np.random.default_rng(seed)
+    col_len = rng.integers(3, 6, size=n)
+    row_idx = _distinct_cols_per_row(rng, col_len, m).astype(np.int64)
+    vals = rng.uniform(0.5, 3.0, size=row_idx.shape[0])
+    row_ptr, col_idx, v = _csc_to_csr(m, n, col_len, row_idx, vals)
+    hi = np.where(rng.random(n) < 0.8, big, rng.uniform(1.0, 3.0, size=n))
+    x_rel = rng.uniform(0.2, 2.8, size=n)
+    lp = LPData(m, n, row_ptr, col_idx, v, rng.uniform(0.5, 2.0, size=n), None, np.full(m, np.inf),
+                np.zeros(n), hi, x_rel, f"covering_large_bounds{seed}")
+    lp.row_lo = rng.uniform(0.3, 0.9, size=m) * lp.matvec(rng.uniform(0.5, 1.0, size=n))
+    cand = rng.choice(n, size=8, replace=False)
+    return Workload(lp, sb_specs(x_rel, cand), "mixed", f"covering m={m} n={n} B=16, bounds {big:g}")
+
+
 def random_lp(seed: int, m: int, n: int, density: float = 0.3, mixed_bounds: bool = True,
               feasible: bool = True, int_values: bool = False) -> LPData:
     """Small random LP with every bound type (free, one-sided and two-sided

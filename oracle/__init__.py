@@ -49,7 +49,8 @@ class Options(C.Structure):
                 ("beta_a", C.c_double), ("theta", C.c_double), ("mnorm_sign", C.c_double),
                 ("restart_to_pdhg_output", C.c_int32), ("power_max_iter", C.c_int32),
                 ("power_tol", C.c_double), ("power_seed", C.c_uint64), ("eps_infeas", C.c_double),
-                ("threads", C.c_int32), ("detect_infeasibility", C.c_int32), ("mutation", C.c_int32)]
+                ("threads", C.c_int32), ("detect_infeasibility", C.c_int32), ("mutation", C.c_int32),
+                ("reduced_cost", C.c_int32)]
 
 
 class _Result(C.Structure):
@@ -71,6 +72,8 @@ def lib():
         _lib.orc_norm2_estimate.argtypes = [i32, i32, vp, vp, vp, i32, d, C.c_uint64, C.POINTER(i32)]
         _lib.orc_scaling.argtypes = [C.POINTER(_Problem), i32, i32, vp, vp]
         _lib.orc_kkt.argtypes = [C.POINTER(_Problem), i32, i32, d, d, d, vp, vp, vp]
+        _lib.orc_kkt_rc.argtypes = [C.POINTER(_Problem), i32, i32, d, d, d, vp, vp, i32, vp]
+        _lib.orc_robust_reduced_cost.argtypes = [i32, vp, vp, vp, vp, vp]
         _lib.orc_solve.restype = i32
         _lib.orc_solve.argtypes = [C.POINTER(_Problem), i32, vp, vp, vp, vp, vp, d, i64,
                                    C.POINTER(Options), vp, vp, vp, vp, C.POINTER(_Result), C.POINTER(d)]
@@ -160,18 +163,19 @@ def solve(lp, specs, tol: float = 1e-4, max_iter: int = 100000, options: Options
                        g("iters", np.int64), g("restarts", np.int32), x, y, eta.value)
 
 
-def kkt(lp, kind: int, var: int, lo: float, hi: float, sign: float, x, y) -> dict:
-    """Relative KKT of (x, y) for one LP in the original space (Eq. stopping)."""
+def kkt(lp, kind: int, var: int, lo: float, hi: float, sign: float, x, y, reduced_cost: int = 0) -> dict:
+    """Relative KKT of (x, y) for one LP in the original space (Eq. stopping);
+    ``reduced_cost`` 1 takes the reduced cost robust to large bounds."""
     h = _Held(lp)
     x, y = _f64(x), _f64(y)
     out = np.zeros(5)
-    lib().orc_kkt(C.byref(h.p), int(kind), int(var), float(lo), float(hi), float(sign),
-                  _ptr(x), _ptr(y), _ptr(out))
+    lib().orc_kkt_rc(C.byref(h.p), int(kind), int(var), float(lo), float(hi), float(sign),
+                     _ptr(x), _ptr(y), int(reduced_cost), _ptr(out))
     return dict(obj=out[0], dual_obj=out[1], rel_primal=out[2], rel_dual=out[3], rel_gap=out[4])
 
 
-def kkt_spec(lp, specs, q: int, x, y) -> dict:
-    return kkt(lp, specs.kind[q], specs.var[q], specs.lo[q], specs.hi[q], specs.sign[q], x, y)
+def kkt_spec(lp, specs, q: int, x, y, reduced_cost: int = 0) -> dict:
+    return kkt(lp, specs.kind[q], specs.var[q], specs.lo[q], specs.hi[q], specs.sign[q], x, y, reduced_cost)
 
 
 def norm2_estimate(lp, max_iter: int = 5000, tol: float = 1e-10, seed: int = 0x5EED):
@@ -208,6 +212,15 @@ def project_barrier(v, a, b):
 
 def project_recession(v, a, b):
     return _elementwise("orc_project_recession", v, a, b)
+
+
+def robust_reduced_cost(v, x, a, b):
+    """Elementwise reduced cost robust to large finite bounds (Sec. 4
+    "Stopping criteria", PDLP's Appendix A variant) of components v at x."""
+    v, x, a, b = _f64(v), _f64(x), _f64(a), _f64(b)
+    out = np.zeros_like(v)
+    lib().orc_robust_reduced_cost(v.shape[0], _ptr(v), _ptr(x), _ptr(a), _ptr(b), _ptr(out))
+    return out
 
 
 def support(v, a, b) -> float:

@@ -38,6 +38,12 @@
  *   R9 recession cone of an interval infinite on both sides is the real line.
  *   R10 eps for infeasibility = the termination tolerance.
  *   R11 restart averages r over the LPs still active at the check.
+ *   R19 the reduced cost of the stopping test is either Pi_B(-c - A^T y) as
+ *      printed (reduced_cost = 0, the default) or the variant robust to large
+ *      finite bounds that the paper's implementation uses (reduced_cost = 1):
+ *      a component counts against a finite bound only where the primal point
+ *      is no farther from that bound than from zero (robust_rc below).  The
+ *      infeasibility tests keep Pi_B in both modes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -77,7 +83,8 @@ typedef struct {
     double eps_infeas;           /* < 0: use tol (reading R10) */
     int32_t threads;
     int32_t detect_infeasibility;
-    int32_t mutation;            /* 0; a test sets 1..7 to plant one known mistake */
+    int32_t mutation;            /* 0; a test sets 1..8 to plant one known mistake */
+    int32_t reduced_cost;        /* 0: Pi_B as printed; 1: robust to large bounds (R19) */
 } orc_options;
 
 typedef struct {
@@ -109,13 +116,15 @@ void orc_default_options(orc_options* o) {
     o->threads = 1;
     o->detect_infeasibility = 1;
     o->mutation = 0;
+    o->reduced_cost = 0;
 }
 
 /* Planted mistakes, used only by the test that checks the pins catch them:
  *  1 x-step sign flipped        2 dual step without its projection term
  *  3 Halpern anchor term dropped 4 reduced cost left out of the dual residual
  *  5 c scaled by 1/D_c           6 support function with a and b swapped
- *  7 M-norm diagonal weights swapped                                         */
+ *  7 M-norm diagonal weights swapped
+ *  8 robust reduced cost paired with the wrong bound                          */
 static int32_t g_mutation = 0;
 void orc_set_mutation(int32_t k) { g_mutation = k; }
 
@@ -150,6 +159,21 @@ static double proj_recession(double v, double a, double b) {
     return 0.0;
 }
 
+/* Reduced cost robust to large finite bounds (Sec. 4 "Stopping criteria":
+ * the paper's implementation replaces Pi_B by the variant of PDLP's
+ * Appendix A; reading R19).  A component v of -c - A^T y pairs with the
+ * upper bound b when positive and with the lower bound a when negative (the
+ * pairing of phi_[a,b]).  It is kept as a reduced cost only where that bound
+ * is finite and the primal value x lies no farther from it than from zero,
+ * |x - bound| <= |x|; otherwise the component is 0 and v stays in the dual
+ * residual c + A^T y + r.  With x on the paired bound this equals Pi_B(v).  */
+static double robust_rc(double v, double x, double a, double b) {
+    if (g_mutation == 8) { double t = a; a = b; b = t; }
+    if (v > 0.0) return (!isinf(b) && fabs(x - b) <= fabs(x)) ? v : 0.0;
+    if (v < 0.0) return (!isinf(a) && fabs(x - a) <= fabs(x)) ? v : 0.0;
+    return 0.0;
+}
+
 /* One term of phi_[a,b](v) = b^T v_+ + a^T v_- (Sec. 3), with 0 * inf = 0. */
 static double support_term(double v, double a, double b) {
     if (g_mutation == 6) { double t = a; a = b; b = t; }
@@ -167,6 +191,10 @@ void orc_project_barrier(int32_t k, const double* v, const double* a, const doub
 }
 void orc_project_recession(int32_t k, const double* v, const double* a, const double* b, double* out) {
     for (int32_t i = 0; i < k; ++i) out[i] = proj_recession(v[i], a[i], b[i]);
+}
+void orc_robust_reduced_cost(int32_t k, const double* v, const double* x, const double* a, const double* b,
+                             double* out) {
+    for (int32_t i = 0; i < k; ++i) out[i] = robust_rc(v[i], x[i], a[i], b[i]);
 }
 double orc_support(int32_t k, const double* v, const double* a, const double* b) {
     double s = 0.0;
@@ -307,10 +335,11 @@ static void lp_vectors(const orc_problem* p, int32_t kind, int32_t var, double l
 
 /* ------------------------------------------------------------------------ */
 /* Eq. stopping: relative KKT of (x, y) in the original space.               */
-/* out = {obj, dual_obj, rel_primal, rel_dual, rel_gap}                      */
+/* out = {obj, dual_obj, rel_primal, rel_dual, rel_gap}; rc_mode 1 takes the */
+/* robust reduced cost (R19) in place of Pi_B.                               */
 /* ------------------------------------------------------------------------ */
 static void kkt_eval(const orc_problem* p, const double* c, const double* xl, const double* xu,
-                     const double* x, const double* y, double* ax, double* aty, double* out) {
+                     const double* x, const double* y, double* ax, double* aty, int rc_mode, double* out) {
     int32_t m = p->m, n = p->n;
     csr_mv(m, p->row_ptr, p->col_idx, p->vals, x, ax);
     csr_tmv(m, n, p->row_ptr, p->col_idx, p->vals, y, aty);
@@ -324,7 +353,8 @@ static void kkt_eval(const orc_problem* p, const double* c, const double* xl, co
     double dres2 = 0.0, c2 = 0.0, ctx = 0.0, phr = 0.0;
     for (int32_t j = 0; j < n; ++j) {
         double q = c[j] + aty[j];
-        double r = proj_barrier(-q, xl[j], xu[j]);   /* r = Pi_B(-c - A^T y) */
+        double r = rc_mode ? robust_rc(-q, x[j], xl[j], xu[j])   /* R19 */
+                           : proj_barrier(-q, xl[j], xu[j]);      /* r = Pi_B(-c - A^T y) */
         double d = g_mutation == 4 ? q : q + r;      /* c + A^T y + r */
         dres2 += d * d;
         c2 += c[j] * c[j];
@@ -342,8 +372,8 @@ static void kkt_eval(const orc_problem* p, const double* c, const double* xl, co
     out[4] = rel_g;
 }
 
-void orc_kkt(const orc_problem* p, int32_t kind, int32_t var, double lo, double hi, double sign,
-             const double* x, const double* y, double* out) {
+void orc_kkt_rc(const orc_problem* p, int32_t kind, int32_t var, double lo, double hi, double sign,
+                const double* x, const double* y, int32_t rc_mode, double* out) {
     int32_t m = p->m, n = p->n;
     double* c = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
     double* xl = c + n;
@@ -351,8 +381,13 @@ void orc_kkt(const orc_problem* p, int32_t kind, int32_t var, double lo, double 
     double* ax = (double*)malloc(sizeof(double) * (size_t)(m + 1));
     double* aty = (double*)malloc(sizeof(double) * (size_t)(n + 1));
     lp_vectors(p, kind, var, lo, hi, sign, c, xl, xu);
-    kkt_eval(p, c, xl, xu, x, y, ax, aty, out);
+    kkt_eval(p, c, xl, xu, x, y, ax, aty, rc_mode, out);
     free(c); free(ax); free(aty);
+}
+
+void orc_kkt(const orc_problem* p, int32_t kind, int32_t var, double lo, double hi, double sign,
+             const double* x, const double* y, double* out) {
+    orc_kkt_rc(p, kind, var, lo, hi, sign, x, y, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -381,6 +416,7 @@ typedef struct {
     const double *Dr, *Dc;
     double *lts, *uts;        /* scaled row bounds */
     double eta;
+    int32_t rc_mode;          /* orc_options.reduced_cost */
 } shared_data;
 
 
@@ -483,7 +519,7 @@ static int32_t evaluate(const shared_data* sd, lp_state* s, double tol, double e
     /* R7: KKT at T(z) in the original space, x = D_c x~, y = D_r y~ */
     for (int32_t j = 0; j < n; ++j) s->xo[j] = proj_box(sd->Dc[j] * s->xh[j], s->xl[j], s->xu[j]);
     for (int32_t i = 0; i < m; ++i) s->yo[i] = sd->Dr[i] * s->yh[i];
-    kkt_eval(p, s->c, s->xl, s->xu, s->xo, s->yo, s->ax, s->aty, s->kkt);
+    kkt_eval(p, s->c, s->xl, s->xu, s->xo, s->yo, s->ax, s->aty, sd->rc_mode, s->kkt);
     for (int k = 0; k < 5; ++k)
         if (isnan(s->kkt[k]) || !isfinite(s->r)) return ORC_NUMERICAL;
     if (s->kkt[2] <= tol && s->kkt[3] <= tol && s->kkt[4] <= tol) return ORC_OPTIMAL;
@@ -658,6 +694,7 @@ int32_t orc_solve(const orc_problem* p, int32_t num_lps, const int32_t* kind, co
     shared_data sd;
     memset(&sd, 0, sizeof(sd));
     sd.p = p;
+    sd.rc_mode = o->reduced_cost ? 1 : 0;
     double* Dr = dvec(m);
     double* Dc = dvec(n);
     orc_scaling(p, o->ruiz_iters, o->pock_chambolle, Dr, Dc);

@@ -310,6 +310,7 @@ void lpb_default_options(lpb_options* o) {
     o->use_graphs = 1;
     o->use_pdl = 1;
     o->stream_priority = 0;
+    o->reduced_cost = LPB_RC_BARRIER;
 }
 
 const char* lpb_last_error(void) { return g_err.c_str(); }
@@ -335,6 +336,7 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
     if (o.precision != LPB_FP64 && o.precision != LPB_MIXED) return fail(LPB_ERR_INVALID_ARG, "bad precision");
     if (o.check_every < 1 || o.ruiz_iters < 0 || o.power_max_iter < 1 || (o.fp64_polish && o.polish_stall_checks < 1) ||
         (o.polish_arith != LPB_POLISH_DFLOAT && o.polish_arith != LPB_POLISH_FP64) || !(o.power_tol >= 0.0) ||
+        (o.reduced_cost != LPB_RC_BARRIER && o.reduced_cost != LPB_RC_ROBUST) ||
         !(o.theta >= 0.0 && o.theta <= 1.0) || !(o.beta_s >= 0.0) || !(o.beta_n >= 0.0) || !(o.beta_a >= 0.0))
         return fail(LPB_ERR_INVALID_ARG, "bad option value");
     // host validation, O(nnz)

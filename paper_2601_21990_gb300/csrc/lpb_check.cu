@@ -51,6 +51,15 @@ __device__ __forceinline__ double proj_barrier(double v, double a, double b) {
     if (hi) return v < 0.0 ? v : 0.0;
     return v;
 }
+// Reduced cost robust to large finite bounds (Sec. 4, stopping criteria;
+// the variant of PDLP's Appendix A): v pairs with b when positive and with a
+// when negative, and is kept only where that bound is finite and
+// |x - bound| <= |x|; elsewhere it is 0 and stays in the dual residual.
+__device__ __forceinline__ double robust_rc(double v, double x, double a, double b) {
+    if (v > 0.0) return !isinf(b) && fabs(x - b) <= fabs(x) ? v : 0.0;
+    if (v < 0.0) return !isinf(a) && fabs(x - a) <= fabs(x) ? v : 0.0;
+    return 0.0;
+}
 // recession cone R_[a,b]; free where both bounds are infinite
 __device__ __forceinline__ double proj_recession(double v, double a, double b) {
     const bool li = isinf(a), hi = isinf(b);
@@ -197,6 +206,7 @@ struct ReduceArgs {
     const double *P0, *P1, *Q0, *Q1, *Q2;
     double* part;
     int restart_to_output;
+    int robust_rc;  // 1: the stopping test takes the robust reduced cost
 };
 
 template <typename T>
@@ -252,11 +262,13 @@ __global__ void k_reduce_rows_n(const ReduceArgs<T> a) {
             const double aty = a.Q0[off] / dc;              // A^T y
             const double q = cj + aty;
             const double r = proj_barrier(-q, lo, hi);      // reduced cost
-            const double d = q + r;
+            // the stopping test's reduced cost; the certificates keep Pi_B
+            const double rs = a.robust_rc ? robust_rc(-q, x, lo, hi) : r;
+            const double d = q + rs;
             s[0] += d * d;
             s[1] += cj * cj;
             s[2] += cj * x;
-            s[3] += support(r, lo, hi);
+            s[3] += support(rs, lo, hi);
             const double dx = (double)a.DX[off];
             s[4] += dx * dx;
             const double anchor = a.restart_to_output ? xh : (double)a.X[off];
@@ -875,6 +887,7 @@ struct ReduceDfArgs {
     const df *P0, *P1, *Q0, *Q1, *Q2;
     double* part;
     int restart_to_output;
+    int robust_rc;  // 1: the stopping test takes the robust reduced cost
 };
 
 // m-side statistics (the same quantities as k_reduce_rows_m); the terms that
@@ -930,11 +943,13 @@ __global__ void k_reduce_n_df(const ReduceDfArgs<TI> a) {
             const df x = df_clamp(it_mul(dc, xh), lo, hi);
             const df q = df_add(cj, df_mul(a.Q0[off], idc));         // c + A^T y
             const df r = df_barrier(df_neg(q), lo, hi);              // reduced cost
-            const float d = df_f(df_add(q, r));
+            // the stopping test's reduced cost; the certificates keep Pi_B
+            const df rs = a.robust_rc ? df_robust_rc(df_neg(q), x, lo, hi) : r;
+            const float d = df_f(df_add(q, rs));
             f_dres2 += d * d;
             f_c2 += cj.hi * cj.hi;
             df_acc(d_ctx, df_mul(cj, x));
-            df_acc(d_phr, df_support(r, lo, hi));
+            df_acc(d_phr, df_support(rs, lo, hi));
             const TI dx = a.DX[off];
             const float dxs = it_f(dx);
             f_dx2 += dxs * dxs;
@@ -998,11 +1013,13 @@ __global__ void k_check_n_df(const ReduceDfArgs<TI> a, const int* __restrict__ r
         const df x = df_clamp(it_mul(dc, xh), lo, hi);
         const df q = df_add(cj, df_mul(q0, idc));                    // c + A^T y
         const df r = df_barrier(df_neg(q), lo, hi);                  // reduced cost
-        const float d = df_f(df_add(q, r));
+        // the stopping test's reduced cost; the certificates keep Pi_B
+        const df rs = a.robust_rc ? df_robust_rc(df_neg(q), x, lo, hi) : r;
+        const float d = df_f(df_add(q, rs));
         f_dres2 += d * d;
         f_c2 += cj.hi * cj.hi;
         df_acc(d_ctx, df_mul(cj, x));
-        df_acc(d_phr, df_support(r, lo, hi));
+        df_acc(d_phr, df_support(rs, lo, hi));
         const TI dx = a.DX[off];
         const float dxs = it_f(dx);
         f_dx2 += dxs * dxs;
@@ -1091,6 +1108,7 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     ra.Q2 = Q2;
     ra.part = partials;
     ra.restart_to_output = d.restart_to_output;
+    ra.robust_rc = d.robust_rc;
     const dim3 rblock(32, kReduceRows);
     if constexpr (kDf) {
         ReduceDfArgs<T> rd{};
@@ -1124,6 +1142,7 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
         rd.Q2 = (const df*)Q2;
         rd.part = partials;
         rd.restart_to_output = d.restart_to_output;
+        rd.robust_rc = d.robust_rc;
         if (nb_m > 0) {
             k_reduce_m_df<T><<<dim3(nb_m, tiles), rblock, 0, s>>>(rd);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;

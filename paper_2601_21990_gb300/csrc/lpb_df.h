@@ -103,6 +103,18 @@ LPB_HD df df_barrier(df v, df a, df b) {
     return v;
 }
 
+LPB_HD df df_abs(df a) { return a.hi < 0.0f ? df_neg(a) : a; }
+
+// Reduced cost robust to large finite bounds (Sec. 4, stopping criteria;
+// the variant of PDLP's Appendix A): v pairs with b when positive and with a
+// when negative, and is kept only where that bound is finite and
+// |x - bound| <= |x|; elsewhere it is 0 and stays in the dual residual.
+LPB_HD df df_robust_rc(df v, df x, df a, df b) {
+    if (v.hi > 0.0f) return !std::isinf(b.hi) && !df_gt(df_abs(df_sub(x, b)), df_abs(x)) ? v : df_zero();
+    if (v.hi < 0.0f) return !std::isinf(a.hi) && !df_gt(df_abs(df_sub(x, a)), df_abs(x)) ? v : df_zero();
+    return df_zero();
+}
+
 // one term b v_+ + a v_- of phi_[a,b](v), with 0 * inf = 0
 LPB_HD df df_support(df v, df a, df b) {
     if (v.hi > 0.0f) return std::isinf(b.hi) ? df{b.hi, 0.0f} : df_mul(b, v);

@@ -288,6 +288,7 @@ CheckData lane_check_data(const lpb_ctx* h, const Lane& ln, int stall_checks) {
     d.mnorm_sign = h->opt.mnorm_sign;
     d.detect_inf = h->opt.detect_infeasibility;
     d.restart_to_output = h->opt.restart_to_pdhg_output;
+    d.robust_rc = h->opt.reduced_cost == LPB_RC_ROBUST;
     d.stall_checks = stall_checks;
     d.check_every = h->opt.check_every;
     d.ctl = ln.ctl;

@@ -202,6 +202,7 @@ struct CheckData {
     ColCheck col;                  // the lane's columns
     double eta, beta_s, beta_n, beta_a, theta, mnorm_sign;
     int detect_inf, restart_to_output;
+    int robust_rc;                 // 1: the stopping test takes the reduced cost robust to large bounds
     int stall_checks;              // 0: no stall test
     int check_every;
     // the lane's restart groups

@@ -26,6 +26,7 @@ OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITERATION_LIMIT, NUMERICAL = range(
 STATUS_NAMES = ["OPTIMAL", "PRIMAL_INFEASIBLE", "DUAL_INFEASIBLE", "ITERATION_LIMIT", "NUMERICAL"]
 FP64, MIXED = 0, 1
 POLISH_DFLOAT, POLISH_FP64 = 0, 1
+RC_BARRIER, RC_ROBUST = 0, 1
 
 # every symbol include/lpb.h declares
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
@@ -54,7 +55,7 @@ class Options(C.Structure):
                 ("detect_infeasibility", C.c_int32), ("profile", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int32), ("fp64_polish", C.c_int32), ("polish_stall_checks", C.c_int32),
                 ("polish_arith", C.c_int32), ("eps_dual", C.c_double), ("use_graphs", C.c_int32),
-                ("use_pdl", C.c_int32), ("stream_priority", C.c_int32)]
+                ("use_pdl", C.c_int32), ("stream_priority", C.c_int32), ("reduced_cost", C.c_int32)]
 
 
 class Spec(C.Structure):

@@ -124,13 +124,13 @@ def highs_dual_infeasible(lp, specs, q):
     return r.status == 2
 
 
-def status_valid(orc, lp, specs, batch, q, status):
+def status_valid(orc, lp, specs, batch, q, status, reduced_cost=0):
     """Independent check of a status that differs from the oracle's: several
     answers can be right for an LP that is feasible only to within the
     tolerance, or that is both primal and dual infeasible."""
     if status == 0:
         r, x, y = batch.result(int(q))
-        k = orc.kkt_spec(lp, specs, int(q), x, y)
+        k = orc.kkt_spec(lp, specs, int(q), x, y, reduced_cost)
         return max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= KKT_TOL
     if status == 1:
         return highs_primal_status(lp, specs, q) == 2
@@ -139,10 +139,10 @@ def status_valid(orc, lp, specs, batch, q, status):
     return False
 
 
-def assert_parity(orc, lp, specs, batch, ref, kkt_lps=None, obj_tol=OBJ_TOL, kkt_tol=KKT_TOL):
+def assert_parity(orc, lp, specs, batch, ref, kkt_lps=None, obj_tol=OBJ_TOL, kkt_tol=KKT_TOL, reduced_cost=0):
     res = batch.results()
     for q in np.nonzero(res["status"] != ref.status)[0]:
-        assert status_valid(orc, lp, specs, batch, q, res["status"][q]), \
+        assert status_valid(orc, lp, specs, batch, q, res["status"][q], reduced_cost), \
             (int(q), int(res["status"][q]), int(ref.status[q]))
     opt = np.nonzero((ref.status == 0) & (res["status"] == 0))[0]
     err = np.abs(res["obj"][opt] - ref.obj[opt]) / (1.0 + np.abs(ref.obj[opt]))
@@ -150,7 +150,7 @@ def assert_parity(orc, lp, specs, batch, ref, kkt_lps=None, obj_tol=OBJ_TOL, kkt
     gpu_opt = np.nonzero(res["status"] == 0)[0]
     for q in (gpu_opt if kkt_lps is None else [q for q in kkt_lps if res["status"][q] == 0]):
         r, x, y = batch.result(int(q))
-        k = orc.kkt_spec(lp, specs, int(q), x, y)
+        k = orc.kkt_spec(lp, specs, int(q), x, y, reduced_cost)
         assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= kkt_tol, (q, k)
         # the library's own reported objective agrees with the oracle's evaluation
         assert r.obj == pytest.approx(k["obj"], rel=1e-6, abs=1e-9)
@@ -169,6 +169,30 @@ def test_sb_small(lpb, orc, precision):
     b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
     res = assert_parity(orc, w.lp, w.specs, b, ref)
     assert np.all(res["iters"] % 64 == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_robust_reduced_cost_large_bounds(lpb, orc, precision):
+    """The stopping test with the reduced cost robust to large bounds (Sec. 4,
+    after Eq. stopping) on covering LPs with 1e10 upper bounds: statuses,
+    objectives and the oracle's robust-mode KKT of each returned point; the
+    robust test ends the batch in well under half the iterations of Pi_B."""
+    w = lpgen.covering_large_bounds(seed=0)
+    ref = oracle_ref(orc, w.lp, w.specs, reduced_cost=1)
+    assert np.all(ref.status == 0)
+    prec = lpb.FP64 if precision == "fp64" else lpb.MIXED
+    h = lpb.Handle(w.lp, precision=prec, reduced_cost=lpb.RC_ROBUST)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    res = assert_parity(orc, w.lp, w.specs, b, ref, reduced_cost=1)
+    assert np.all(res["status"] == 0)
+    # the reported dual objective is the robust one
+    for q in range(len(w.specs)):
+        r, x, y = b.result(q)
+        k = orc.kkt_spec(w.lp, w.specs, q, x, y, 1)
+        assert r.dual_obj == pytest.approx(k["dual_obj"], rel=1e-6, abs=1e-6)
+    h0 = lpb.Handle(w.lp, precision=prec)
+    res0 = h0.solve(w.specs, tol=GPU_TOL, max_iter=30000).results()
+    assert res["iters"].sum() < 0.5 * res0["iters"].sum(), (res["iters"], res0["iters"])
 
 
 def test_sb_powerlaw_full_size(lpb, orc):

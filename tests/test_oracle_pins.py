@@ -49,6 +49,24 @@ def test_support_function_hand_values(oracle_lib):
     assert o.support([1.0], [0.0], [INF]) == INF
 
 
+def test_robust_reduced_cost_hand_vectors(oracle_lib):
+    # v > 0 pairs with the upper bound b, v < 0 with the lower bound a; kept
+    # only where that bound is finite and |x - bound| <= |x|
+    v = [1.0, 1.0, -1.0, -1.0, 0.0, 2.0, 3.0, -2.0, 1.0]
+    x = [0.0, 9.0, 0.0, 3.0, 5.0, 5.0, -4.0, -4.0, 2.0]
+    a = [0.0, 0.0, 0.0, -1e300, 0.0, 0.0, -5.0, -5.0, -INF]
+    b = [1e10, 10.0, 1e10, 10.0, 10.0, 10.0, -3.0, -3.0, INF]
+    np.testing.assert_array_equal(oracle_lib.robust_reduced_cost(v, x, a, b),
+                                  [0.0, 1.0, -1.0, 0.0, 0.0, 2.0, 3.0, -2.0, 0.0])
+    # with x on the bound v pairs with, it is Pi_B(v)
+    va = np.array([0.7, -0.3, 1.5, -2.5])
+    lo = np.array([-2.0, -2.0, 1.0, 1.0])
+    hi = np.array([3.0, 3.0, 4.0, 4.0])
+    xs = np.where(va > 0, hi, lo)
+    np.testing.assert_array_equal(oracle_lib.robust_reduced_cost(va, xs, lo, hi),
+                                  oracle_lib.project_barrier(va, lo, hi))
+
+
 def test_splitmix64_published_outputs(oracle_lib):
     # SplitMix64 seeded with 0 (Steele, Lea, Flood 2014; reference code by Vigna)
     assert oracle_lib.splitmix64_at(0, 0) == 0xE220A8397B1DCDAF
@@ -70,6 +88,58 @@ def test_kkt_handworked_golden(oracle_lib):
                 assert k[key] == want, (case["name"], key)
             else:
                 assert k[key] == pytest.approx(want, abs=1e-14, rel=1e-12), (case["name"], key)
+
+
+def _robust_cases():
+    g = json.load(open(os.path.join(HERE, "golden", "kkt_robust_handworked.json")))
+    lpd = g["lp"]
+    for case in g["cases"]:
+        lp = lpgen.from_dense(lpd["A"], lpd["c"], [_f(v) for v in lpd["row_lo"]],
+                              [_f(v) for v in lpd["row_hi"]], [_f(v) for v in case["var_lo"]],
+                              [_f(v) for v in case["var_hi"]])
+        yield case, lp
+
+
+def test_kkt_robust_reduced_cost_handworked_golden(oracle_lib):
+    for case, lp in _robust_cases():
+        for mode, want in case["modes"].items():
+            k = oracle_lib.kkt(lp, 0, 0, 0.0, 0.0, 1.0, case["x"], case["y"], reduced_cost=int(mode))
+            for key, v in want.items():
+                assert k[key] == pytest.approx(_f(v), abs=1e-14, rel=1e-12), (case["name"], mode, key)
+
+
+def test_robust_reduced_cost_knapsack_with_huge_bounds(oracle_lib):
+    """Upper bounds of 1e10 that no optimum reaches: the robust stopping test
+    meets a tight tolerance at the greedy closed form."""
+    rng = np.random.default_rng(5)
+    n = 8
+    a = rng.uniform(0.5, 3, n)
+    c = rng.uniform(0.5, 3, n)
+    b = 4.0
+    i = int(np.argmin(c / a))
+    f = c[i] * b / a[i]  # all coverage from the cheapest variable per unit
+    lp = lpgen.from_dense(a[None, :], c, [b], [INF], np.zeros(n), np.full(n, 1e10))
+    r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-8, max_iter=200000, check_every=16, reduced_cost=1)
+    assert r.status[0] == 0
+    assert r.obj[0] == pytest.approx(f, rel=1e-6)
+    k = oracle_lib.kkt(lp, 0, 0, 0.0, 0.0, 1.0, r.x[0], r.y[0], reduced_cost=1)
+    assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-8
+
+
+def test_robust_reduced_cost_large_bounds_against_highs(oracle_lib):
+    """Covering LPs whose 1e10 upper bounds no optimum reaches: with the
+    robust reduced cost every child meets 1e-7 at HiGHS's objective; with
+    Pi_B as printed, the bounds' share of the dual objective keeps the gap
+    open under the same iteration cap."""
+    w = lpgen.covering_large_bounds(seed=0)
+    r = oracle_lib.solve(w.lp, w.specs, tol=1e-7, max_iter=50000, lockstep=0, threads=4, reduced_cost=1)
+    assert np.all(r.status == 0)
+    for q in range(len(w.specs)):
+        st, f = highs_solve(w.lp, w.specs, q)
+        assert st == 0 and abs(r.obj[q] - f) / (1 + abs(f)) <= 1e-6, (q, r.obj[q], f)
+    r0 = oracle_lib.solve(w.lp, w.specs.subset(range(4)), tol=1e-7, max_iter=50000, lockstep=0, threads=4)
+    assert np.all(r0.status == 3)
+    assert np.all(r0.rel_gap > 1e-6)
 
 
 # ---------------------------------------------------------------------------
@@ -397,6 +467,11 @@ def _pins_pass(o, mutation):
             for key in ("obj", "dual_obj", "rel_primal", "rel_dual", "rel_gap"):
                 if abs(k[key] - _f(case[key])) > 1e-12:
                     return False
+        for case, lp in _robust_cases():
+            k = o.kkt(lp, 0, 0, 0.0, 0.0, 1.0, case["x"], case["y"], reduced_cost=1)
+            for key, v in case["modes"]["1"].items():
+                if abs(k[key] - _f(v)) > 1e-12 * max(1.0, abs(_f(v))):
+                    return False
         # nonexpansiveness on one LP
         lp, eta = _t_data(0)
         rng = np.random.default_rng(0)
@@ -427,6 +502,6 @@ def test_pins_pass_without_mutation(oracle_lib):
     assert _pins_pass(oracle_lib, 0)
 
 
-@pytest.mark.parametrize("mutation", range(1, 8))
+@pytest.mark.parametrize("mutation", range(1, 9))
 def test_planted_mistakes_are_caught(oracle_lib, mutation):
     assert not _pins_pass(oracle_lib, mutation)
