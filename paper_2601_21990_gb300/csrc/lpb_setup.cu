@@ -341,31 +341,68 @@ __global__ void k_power_init(double* v, int n, uint64_t seed) {
         v[j] = 2.0 * ((double)(splitmix64(seed, (uint64_t)j) >> 11) * 0x1.0p-53) - 1.0;
 }
 
-// y = M x, warp per row, FP64
-__global__ void k_spmv64(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
-                         int rows, const double* __restrict__ x, double* __restrict__ y) {
-    const int warps = gridDim.x * blockDim.x / 32;
-    const int lane = threadIdx.x & 31;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < rows; i += warps) {
-        double acc = 0.0;
-        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) acc += v[e] * x[ci[e]];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
-        if (lane == 0) y[i] = acc;
-    }
+// One product of A~^T A~ takes two launches of k_power_spmv.  Each leaves
+// the squared norm of its result as one partial sum per block (the grid is
+// fixed at kPowBlocks, so the rows each block covers and the order of every
+// sum are the same on every run), and the next launch adds those partials in
+// a fixed order itself.  The normalisation v = w / ||w|| of the iteration is
+// applied after the forward product, u = (A~ w) / ||w||, so no launch writes
+// v and none only reduces.
+constexpr int kPowBlocks = 512;
+constexpr int kPowThreads = 256;
+constexpr int kPowGroup = 8;  // lanes per row
+
+// sqrt of the sum of the kPowBlocks partials, in every thread of the block
+__device__ __forceinline__ double partials_norm(const double* __restrict__ part, double* sh) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kPowBlocks; i += blockDim.x) acc += part[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) sh[32] = sqrt(t);
+    __syncthreads();
+    return sh[32];
 }
 
-// v = w / sqrt(*nw2) when the norm is positive; records sqrt(nw2) and
-// sqrt(est2) in the history at `it`
-__global__ void k_power_normalize(double* __restrict__ v, const double* __restrict__ w, int n,
-                                  const double* __restrict__ est2, const double* __restrict__ nw2,
-                                  double* __restrict__ hist_est, double* __restrict__ hist_nw, int it) {
-    double nw = sqrt(*nw2);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        hist_est[it] = sqrt(*est2);
-        hist_nw[it] = nw;
+// y = M x (divided by ||x|| when `normalize`), kPowGroup lanes per row, and
+// part_y[block] = the block's sum of y_i^2.  ||x|| comes from part_x; block 0
+// records it at hist[slot] when hist is given.
+__global__ void __launch_bounds__(kPowThreads) k_power_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
+                                                            const double* __restrict__ v, int rows,
+                                                            const double* __restrict__ x,
+                                                            const double* __restrict__ part_x, int normalize,
+                                                            double* __restrict__ y, double* __restrict__ part_y,
+                                                            double* __restrict__ hist, int slot) {
+    __shared__ double sh[33];
+    double nx = 1.0;
+    if (normalize || (hist && blockIdx.x == 0)) {
+        nx = partials_norm(part_x, sh);
+        if (hist && blockIdx.x == 0 && threadIdx.x == 0) hist[slot] = nx;
     }
-    if (!(nw > 0.0)) return;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) v[j] = w[j] / nw;
+    constexpr int kRowsPerWarp = 32 / kPowGroup;
+    const int lane = threadIdx.x % kPowGroup, sub = (threadIdx.x & 31) / kPowGroup;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
+    double sq = 0.0;  // the group's rows in order, in its first lane
+    // the loop bound is the same for the whole warp, so every lane reaches the shuffles
+    for (int base = warp * kRowsPerWarp; base < rows; base += warps * kRowsPerWarp) {
+        const int i = base + sub;
+        double acc = 0.0;
+        if (i < rows)
+            for (int e = rp[i] + lane; e < rp[i + 1]; e += kPowGroup) acc += v[e] * x[ci[e]];
+        for (int o = kPowGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, kPowGroup);
+        if (lane == 0 && i < rows) {
+            const double yi = !normalize ? acc : (nx > 0.0 ? acc / nx : 0.0);
+            y[i] = yi;
+            sq += yi * yi;
+        }
+    }
+    const double t = block_sum(sq, sh);
+    if (threadIdx.x == 0) part_y[blockIdx.x] = t;
+}
+
+// hist[slot] = sqrt of the sum of the kPowBlocks partials (one block)
+__global__ void k_power_record(const double* __restrict__ part, double* __restrict__ hist, int slot) {
+    __shared__ double sh[33];
+    const double nx = partials_norm(part, sh);
+    if (threadIdx.x == 0) hist[slot] = nx;
 }
 
 inline int grid_for(long long work, int threads, int cap = 4096) {
@@ -565,6 +602,10 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
     return cudaFreeAsync(part, s);
 }
 
+size_t power_work_doubles(int m, int n, int max_iter) {
+    return (size_t)n + (size_t)(m > 0 ? m : 1) + 2 * (size_t)kPowBlocks + 2 * ((size_t)max_iter + 1);
+}
+
 // Power iteration on A~^T A~: sigma_est = ||A~ v|| for unit v.  Stops at the
 // first product where the estimate moves by <= tol relative, or when
 // ||A~^T A~ v|| = 0, or after max_iter products.  The host looks at the
@@ -573,23 +614,20 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
                        double* est_out, int* iters_out, cudaStream_t s) {
     const int m = a.rows, n = a.cols;
-    // work layout: v (n), w (n), u (m), est2, nw2, v2, hist_est (max_iter+1), hist_nw (max_iter+1), part
-    double* v = work;
-    double* w = v + n;
+    // work layout (power_work_doubles): w (n), u (m), part_u, part_w (kPowBlocks each),
+    // hist_est, hist_nw (max_iter + 1 each); w starts as the unnormalised start vector
+    double* w = work;
     double* u = w + n;
-    double* est2 = u + (m > 0 ? m : 1);
-    double* nw2 = est2 + 1;
-    double* v2 = nw2 + 1;
-    double* hist_est = v2 + 1;
+    double* part_u = u + (m > 0 ? m : 1);
+    double* part_w = part_u + kPowBlocks;
+    double* hist_est = part_w + kPowBlocks;
     double* hist_nw = hist_est + (max_iter + 1);
-    double* part = hist_nw + (max_iter + 1);
     cudaError_t e;
     *est_out = 0.0;
     *iters_out = 0;
     if (m == 0 || a.nnz == 0) return cudaSuccess;
-    k_power_init<<<grid_for(n, 256), 256, 0, s>>>(v, n, seed);
-    if ((e = two_stage(v, nullptr, n, 0, v2, part, s)) != cudaSuccess) return e;
-    k_power_normalize<<<grid_for(n, 256), 256, 0, s>>>(v, v, n, v2, v2, hist_est, hist_nw, 0);
+    k_power_init<<<grid_for(n, 256), 256, 0, s>>>(w, n, seed);
+    k_sum_stage1<<<kPowBlocks, kSumThreads, 0, s>>>(w, nullptr, n, 0, part_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     constexpr int kChunk = 64;
     std::vector<double> he(kChunk), hn(kChunk);
@@ -597,12 +635,13 @@ cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, ui
     for (int base = 1; base <= max_iter; base += kChunk) {
         const int last = base + kChunk - 1 < max_iter ? base + kChunk - 1 : max_iter;
         for (int it = base; it <= last; ++it) {
-            k_spmv64<<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a.v64, m, v, u);
-            two_stage(u, nullptr, m, 0, est2, part, s);
-            k_spmv64<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at.v64, n, u, w);
-            two_stage(w, nullptr, n, 0, nw2, part, s);
-            k_power_normalize<<<grid_for(n, 256), 256, 0, s>>>(v, w, n, est2, nw2, hist_est, hist_nw, it);
+            // u = A~ w / ||w|| (records ||w|| of the previous product), then w = A~^T u (records ||u||)
+            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, w, part_w, 1, u, part_u,
+                                                            hist_nw, it - 1);
+            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, u, part_u, 0, w, part_w,
+                                                            hist_est, it);
         }
+        k_power_record<<<1, kPowThreads, 0, s>>>(part_w, hist_nw, last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int cnt = last - base + 1;
         if ((e = cudaMemcpyAsync(he.data(), hist_est + base, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
