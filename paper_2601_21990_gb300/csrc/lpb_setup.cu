@@ -348,9 +348,16 @@ __global__ void k_power_init(double* v, int n, uint64_t seed) {
 // a fixed order itself.  The normalisation v = w / ||w|| of the iteration is
 // applied after the forward product, u = (A~ w) / ||w||, so no launch writes
 // v and none only reduces.
-constexpr int kPowBlocks = 512;
+#ifndef LPB_POW_BLOCKS
+#define LPB_POW_BLOCKS 512
+#endif
+#ifndef LPB_POW_GROUP
+#define LPB_POW_GROUP 8
+#endif
+constexpr int kPowBlocks = LPB_POW_BLOCKS;
 constexpr int kPowThreads = 256;
-constexpr int kPowGroup = 8;  // lanes per row
+constexpr int kPowGroup = LPB_POW_GROUP;  // lanes per row
+static_assert(kPowGroup >= 1 && kPowGroup <= 32 && (kPowGroup & (kPowGroup - 1)) == 0, "lanes per row: a power of 2");
 
 // sqrt of the sum of the kPowBlocks partials, in every thread of the block
 __device__ __forceinline__ double partials_norm(const double* __restrict__ part, double* sh) {
