@@ -341,11 +341,12 @@ __global__ void k_power_init(double* v, int n, uint64_t seed) {
         v[j] = 2.0 * ((double)(splitmix64(seed, (uint64_t)j) >> 11) * 0x1.0p-53) - 1.0;
 }
 
-// One product of A~^T A~ takes two launches of k_power_spmv.  Each leaves
-// the squared norm of its result as one partial sum per block (the grid is
-// fixed at kPowBlocks, so the rows each block covers and the order of every
-// sum are the same on every run), and the next launch adds those partials in
-// a fixed order itself.  The normalisation v = w / ||w|| of the iteration is
+// One product of A~^T A~ takes two launches of k_power_spmv.  Each block
+// leaves its share of the squared norm of the result as one partial; the
+// last block to finish (an atomic ticket, no waiting) adds the partials in
+// block order and writes the norm to a scalar the next launch reads.  The
+// grid is fixed at kPowBlocks, so the rows each block covers and the order of
+// every sum are the same on every run.  The normalisation v = w / ||w|| is
 // applied after the forward product, u = (A~ w) / ||w||, so no launch writes
 // v and none only reduces.
 #ifndef LPB_POW_BLOCKS
@@ -359,31 +360,42 @@ constexpr int kPowThreads = 256;
 constexpr int kPowGroup = LPB_POW_GROUP;  // lanes per row
 static_assert(kPowGroup >= 1 && kPowGroup <= 32 && (kPowGroup & (kPowGroup - 1)) == 0, "lanes per row: a power of 2");
 
-// sqrt of the sum of the kPowBlocks partials, in every thread of the block
-__device__ __forceinline__ double partials_norm(const double* __restrict__ part, double* sh) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < kPowBlocks; i += blockDim.x) acc += part[i];
-    const double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) sh[32] = sqrt(t);
+// The last of the grid's blocks to call this (after writing part[blockIdx.x])
+// sets *nrm = sqrt(sum of the partials in block order), records it at
+// hist[slot] when hist is given, and rearms the ticket.
+__device__ __forceinline__ void finish_norm(double* part, unsigned* __restrict__ ticket,
+                                            double* __restrict__ nrm, double* __restrict__ hist, int slot,
+                                            double* sh) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    return sh[32];
+    if (!last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(tot);
+        *nrm = nr;
+        if (hist) hist[slot] = nr;
+        *ticket = 0u;
+    }
 }
 
-// y = M x (divided by ||x|| when `normalize`), kPowGroup lanes per row, and
-// part_y[block] = the block's sum of y_i^2.  ||x|| comes from part_x; block 0
-// records it at hist[slot] when hist is given.
+// y = M x (divided by *nrm_x when nrm_x is given), kPowGroup lanes per row;
+// *nrm_y = ||y|| (and hist[slot] = ||y|| when hist is given).
 __global__ void __launch_bounds__(kPowThreads) k_power_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                                             const double* __restrict__ v, int rows,
                                                             const double* __restrict__ x,
-                                                            const double* __restrict__ part_x, int normalize,
-                                                            double* __restrict__ y, double* __restrict__ part_y,
+                                                            const double* __restrict__ nrm_x,
+                                                            double* __restrict__ y, double* part,
+                                                            unsigned* __restrict__ ticket, double* __restrict__ nrm_y,
                                                             double* __restrict__ hist, int slot) {
-    __shared__ double sh[33];
-    double nx = 1.0;
-    if (normalize || (hist && blockIdx.x == 0)) {
-        nx = partials_norm(part_x, sh);
-        if (hist && blockIdx.x == 0 && threadIdx.x == 0) hist[slot] = nx;
-    }
+    __shared__ double sh[32];
+    const double nx = nrm_x ? *nrm_x : 1.0;
     constexpr int kRowsPerWarp = 32 / kPowGroup;
     const int lane = threadIdx.x % kPowGroup, sub = (threadIdx.x & 31) / kPowGroup;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
@@ -396,20 +408,26 @@ __global__ void __launch_bounds__(kPowThreads) k_power_spmv(const int* __restric
             for (int e = rp[i] + lane; e < rp[i + 1]; e += kPowGroup) acc += v[e] * x[ci[e]];
         for (int o = kPowGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, kPowGroup);
         if (lane == 0 && i < rows) {
-            const double yi = !normalize ? acc : (nx > 0.0 ? acc / nx : 0.0);
+            const double yi = !nrm_x ? acc : (nx > 0.0 ? acc / nx : 0.0);
             y[i] = yi;
             sq += yi * yi;
         }
     }
     const double t = block_sum(sq, sh);
-    if (threadIdx.x == 0) part_y[blockIdx.x] = t;
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    finish_norm(part, ticket, nrm_y, hist, slot, sh);
 }
 
-// hist[slot] = sqrt of the sum of the kPowBlocks partials (one block)
-__global__ void k_power_record(const double* __restrict__ part, double* __restrict__ hist, int slot) {
-    __shared__ double sh[33];
-    const double nx = partials_norm(part, sh);
-    if (threadIdx.x == 0) hist[slot] = nx;
+// *nrm = ||x|| with the same two-level fixed-order sum
+__global__ void __launch_bounds__(kPowThreads) k_power_norm(const double* __restrict__ x, int count,
+                                                            double* part, unsigned* __restrict__ ticket,
+                                                            double* __restrict__ nrm) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) acc += x[i] * x[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    finish_norm(part, ticket, nrm, nullptr, 0, sh);
 }
 
 inline int grid_for(long long work, int threads, int cap = 4096) {
@@ -610,7 +628,7 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
 }
 
 size_t power_work_doubles(int m, int n, int max_iter) {
-    return (size_t)n + (size_t)(m > 0 ? m : 1) + 2 * (size_t)kPowBlocks + 2 * ((size_t)max_iter + 1);
+    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + 3 + 2 * ((size_t)max_iter + 1);
 }
 
 // Power iteration on A~^T A~: sigma_est = ||A~ v|| for unit v.  Stops at the
@@ -621,20 +639,23 @@ size_t power_work_doubles(int m, int n, int max_iter) {
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
                        double* est_out, int* iters_out, cudaStream_t s) {
     const int m = a.rows, n = a.cols;
-    // work layout (power_work_doubles): w (n), u (m), part_u, part_w (kPowBlocks each),
-    // hist_est, hist_nw (max_iter + 1 each); w starts as the unnormalised start vector
+    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks), ||u||, ||w||, the
+    // ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the unnormalised start vector
     double* w = work;
     double* u = w + n;
-    double* part_u = u + (m > 0 ? m : 1);
-    double* part_w = part_u + kPowBlocks;
-    double* hist_est = part_w + kPowBlocks;
+    double* part = u + (m > 0 ? m : 1);
+    double* nrm_u = part + kPowBlocks;
+    double* nrm_w = nrm_u + 1;
+    unsigned* ticket = reinterpret_cast<unsigned*>(nrm_w + 1);
+    double* hist_est = nrm_w + 2;
     double* hist_nw = hist_est + (max_iter + 1);
     cudaError_t e;
     *est_out = 0.0;
     *iters_out = 0;
     if (m == 0 || a.nnz == 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     k_power_init<<<grid_for(n, 256), 256, 0, s>>>(w, n, seed);
-    k_sum_stage1<<<kPowBlocks, kSumThreads, 0, s>>>(w, nullptr, n, 0, part_w);
+    k_power_norm<<<kPowBlocks, kPowThreads, 0, s>>>(w, n, part, ticket, nrm_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     constexpr int kChunk = 64;
     std::vector<double> he(kChunk), hn(kChunk);
@@ -642,13 +663,12 @@ cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, ui
     for (int base = 1; base <= max_iter; base += kChunk) {
         const int last = base + kChunk - 1 < max_iter ? base + kChunk - 1 : max_iter;
         for (int it = base; it <= last; ++it) {
-            // u = A~ w / ||w|| (records ||w|| of the previous product), then w = A~^T u (records ||u||)
-            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, w, part_w, 1, u, part_u,
-                                                            hist_nw, it - 1);
-            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, u, part_u, 0, w, part_w,
+            // u = A~ w / ||w|| (records ||u||), then w = A~^T u (records ||w||)
+            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, w, nrm_w, u, part, ticket, nrm_u,
                                                             hist_est, it);
+            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, u, nullptr, w, part, ticket,
+                                                            nrm_w, hist_nw, it);
         }
-        k_power_record<<<1, kPowThreads, 0, s>>>(part_w, hist_nw, last);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int cnt = last - base + 1;
         if ((e = cudaMemcpyAsync(he.data(), hist_est + base, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
