@@ -91,6 +91,21 @@ def test_default_options(lib):
     assert o.device == -1 and o.cuda_stream is None
 
 
+def test_option_validation_rejects_bad_values(lib):
+    """Option checks run before any device call, so they need no GPU."""
+    from paper_2601_21990_gb300 import lpb
+
+    assert lpb.lpb_default_options().reduced_cost == lpb.RC_BARRIER
+    ok = dict(m=1, n=2, row_ptr=[0, 2], col_idx=[0, 1], vals=[1.0, 1.0], c=[1.0, 1.0], row_lo=[0.0],
+              row_hi=[1.0], var_lo=[0.0, 0.0], var_hi=[1.0, 1.0])
+    bad = [dict(reduced_cost=2), dict(reduced_cost=-1), dict(polish_arith=5), dict(precision=7),
+           dict(check_every=0), dict(theta=1.5), dict(beta_s=-0.1), dict(power_max_iter=0)]
+    for b in bad:
+        with pytest.raises(lpb.LpbError) as e:
+            lpb.lpb_create(**ok, options=lpb.lpb_default_options(**b))
+        assert e.value.code == lpb.LPB_ERR_INVALID_ARG, b
+
+
 def test_struct_layouts_match_header(tmp_path):
     from paper_2601_21990_gb300 import lpb
 
