@@ -23,17 +23,9 @@ template <> struct Vec<float> { static constexpr int V = 4; };
 template <> struct Vec<double> { static constexpr int V = 2; };
 template <> struct Vec<dfloat> { static constexpr int V = 2; };
 
-__device__ __forceinline__ void ldg_d(const float* p, double (&r)[4]) {
-    float4 u = __ldg(reinterpret_cast<const float4*>(p));
-    r[0] = u.x; r[1] = u.y; r[2] = u.z; r[3] = u.w;
-}
 __device__ __forceinline__ void ldg_d(const double* p, double (&r)[2]) {
     double2 u = __ldg(reinterpret_cast<const double2*>(p));
     r[0] = u.x; r[1] = u.y;
-}
-__device__ __forceinline__ void st_d(double* p, const double (&r)[4]) {
-    reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
 }
 __device__ __forceinline__ void st_d(double* p, const double (&r)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);

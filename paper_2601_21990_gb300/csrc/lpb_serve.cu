@@ -123,7 +123,7 @@ void free_request_results(Request& r, cudaStream_t s) {
 }
 
 // Device buffers and admission of request r into its matrix's FP32 lane.
-lpb_err admit(lpb_server* srv, Matrix& M, Request& r, int gid, int slot0, const double* warm_src_x,
+lpb_err admit(Matrix& M, Request& r, int gid, int slot0, const double* warm_src_x,
               const double* warm_src_y) {
     lpb_ctx* h = M.h;
     cudaStream_t s = h->stream;
@@ -209,7 +209,7 @@ lpb_err admit_pending(lpb_server* srv, Matrix& M, bool& did_work) {
             M.pending.pop_front();
         }
         const bool busy = M.lane32.ncol > 0 || M.lanep.ncol > 0;
-        lpb_err rc = admit(srv, M, *r, gid, slot0, wsx, wsy);
+        lpb_err rc = admit(M, *r, gid, slot0, wsx, wsy);
         std::lock_guard<std::mutex> lk(srv->mu);
         if (rc != LPB_OK) {
             r->state = kFailed;
@@ -239,7 +239,7 @@ lpb_err admit_pending(lpb_server* srv, Matrix& M, bool& did_work) {
 }
 
 // Launches one interval on each of M's lanes with work (async on M's stream).
-lpb_err launch(lpb_server* srv, Matrix& M, lpb_server_stats& add, lpb_profile& prof) {
+lpb_err launch(Matrix& M, lpb_server_stats& add, lpb_profile& prof) {
     const int ce = M.h->opt.check_every;
     if (M.lane32.ncol > 0) {
         add.column_iters += (int64_t)M.lane32.ncol * ce;
@@ -352,7 +352,7 @@ lpb_err step_matrix(lpb_server* srv, Matrix& M, int mi, bool& did_work) {
         did_work = true;
     }
     if ((rc = admit_pending(srv, M, did_work)) != LPB_OK) return rc;
-    if ((rc = launch(srv, M, add, prof)) != LPB_OK) return rc;
+    if ((rc = launch(M, add, prof)) != LPB_OK) return rc;
     if (M.in_flight) {
         mark_in_flight(srv, +1);
         did_work = true;
