@@ -354,6 +354,39 @@ def test_mixed_bound_lps_against_highs(oracle_lib, seed):
         assert abs(r.obj[0] - f) / (1 + abs(f)) <= 1e-6
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_robust_reduced_cost_mixed_bounds_against_highs(oracle_lib, seed):
+    """Robust-mode stopping on every bound type (free, one-sided and fixed
+    variables; equality, ranged and one-sided rows) reaches HiGHS's optimum
+    and the same status; with the far side of some boxes moved out to 1e9 the
+    optimum is unchanged when HiGHS says so."""
+    lp = lpgen.random_lp(seed, 4 + seed % 5, 6 + seed % 4)
+    sp = lpgen.base_specs(1)
+    st, f = highs_solve(lp, sp, 0)
+    r = oracle_lib.solve(lp, sp, tol=1e-8, max_iter=400000, check_every=16, reduced_cost=1)
+    assert r.status[0] == {0: 0, 2: 1, 3: 2}[st]
+    if st != 0:
+        return
+    assert abs(r.obj[0] - f) / (1 + abs(f)) <= 1e-6
+    k = oracle_lib.kkt(lp, 0, 0, 0.0, 0.0, 1.0, r.x[0], r.y[0], reduced_cost=1)
+    assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-8
+    # widen the inactive side of each two-sided box to 1e9
+    x = r.x[0]
+    lo, hi = lp.var_lo.copy(), lp.var_hi.copy()
+    two = np.isfinite(lo) & np.isfinite(hi) & (hi > lo)
+    far_hi = two & (hi - x > 1e-3)
+    far_lo = two & (x - lo > 1e-3) & ~far_hi
+    hi[far_hi] = 1e9
+    lo[far_lo] = -1e9
+    wide = lpgen.LPData(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.vals, lp.c, lp.row_lo, lp.row_hi, lo, hi)
+    st2, f2 = highs_solve(wide, sp, 0)
+    if st2 != 0:
+        return
+    r2 = oracle_lib.solve(wide, sp, tol=1e-8, max_iter=400000, check_every=16, reduced_cost=1)
+    assert r2.status[0] == 0
+    assert abs(r2.obj[0] - f2) / (1 + abs(f2)) <= 1e-6
+
+
 @pytest.mark.parametrize("seed", range(10))
 def test_infeasibility_status_against_highs(oracle_lib, seed):
     lp = lpgen.random_lp(seed, 5, 7, feasible=False)
