@@ -374,6 +374,28 @@ def test_ragged_and_multi_tile_batches(lpb, orc):
     assert np.max(np.abs(b200["obj"] - ref16.obj[idx]) / (1 + np.abs(ref16.obj[idx]))) <= OBJ_TOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_halpern_trajectory_closed_form(lpb, precision):
+    """The iteration itself, not only its limit: one variable, no rows, box
+    [-1, 1], cost 1e-3, so eta = 0.998, w = 1 and T(z) = z - delta with
+    delta = 0.998e-3.  Eq. mainiter then gives z^k = z^0 - k delta in closed
+    form, and the point evaluated at the K-th check is z^0 - K delta.
+    Restarts off, a check every iteration, the solve ends at the limit K."""
+    lp = lpgen.from_dense(np.zeros((0, 1)), [1e-3], [], [], [-1.0], [1.0])
+    prec = lpb.FP64 if precision == "fp64" else lpb.MIXED
+    h = lpb.Handle(lp, precision=prec, check_every=1, detect_infeasibility=0, beta_s=0.0, beta_n=0.0,
+                   beta_a=1e9, fp64_polish=0)
+    eta, est, its = h.info()
+    assert eta == 0.998
+    for K in (1, 2, 7, 50, 400):
+        b = h.solve(lpgen.base_specs(1), tol=1e-12, max_iter=K, warm_x=np.array([0.5]))
+        r, x, y = b.result(0)
+        assert r.status == lpb.ITERATION_LIMIT and r.iters == K and r.restarts == 0
+        # FP32 iterates round once per step (at most about 6e-8 each); a wrong
+        # Halpern weight, anchor or reflection is off by about delta per step
+        assert x[0] == pytest.approx(0.5 - K * 0.998e-3, abs=1e-12 if precision == "fp64" else 1e-4)
+
+
 def test_box_lp_without_rows(lpb):
     rng = np.random.default_rng(4)
     n = 37

@@ -209,6 +209,31 @@ def test_T_is_nonexpansive_in_M_norm(oracle_lib):
                 assert after <= before * (1 + 1e-12) + 1e-12
 
 
+def _translation_lp():
+    """One variable, no rows, box [-1, 1], cost 1e-3: with no rows ||A~|| = 0,
+    so eta = 0.998 and w = 1 (readings R2, R3), tau = 0.998, and the PDHG
+    operator is the translation T(z) = z - delta, delta = tau * 1e-3, until
+    the box is reached."""
+    return lpgen.from_dense(np.zeros((0, 1)), [1e-3], [], [], [-1.0], [1.0])
+
+
+def test_halpern_trajectory_closed_form(oracle_lib):
+    """Eq. mainiter on a translation, solved in closed form: with
+    z^{k+1} = (k+1)/(k+2) (2 T(z^k) - z^k) + z^0/(k+2) and T(z) = z - delta,
+    (k+2) z^{k+1} = (k+1) (z^k - 2 delta) + z^0 gives z^k = z^0 - k delta, so
+    the point evaluated at the K-th check, T(z^{K-1}), is z^0 - K delta.
+    Restarts are switched off (beta_s = beta_n = 0, beta_a = 1e9) and every
+    iteration is a check, so the solve stops at the iteration limit K."""
+    lp = _translation_lp()
+    delta = 0.998e-3
+    for K in (1, 2, 3, 7, 50, 400):
+        r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-12, max_iter=K, check_every=1,
+                             detect_infeasibility=0, beta_s=0.0, beta_n=0.0, beta_a=1e9,
+                             warm_x=[0.5], warm_y=np.zeros(0))
+        assert r.status[0] == 3 and r.iters[0] == K and r.restarts[0] == 0
+        assert r.x[0][0] == pytest.approx(0.5 - K * delta, abs=1e-14)
+
+
 def test_fixed_point_residual_zero_at_optimum(oracle_lib):
     """At a primal-dual optimum z*, T(z*) = z* (hand LP of the KKT golden)."""
     o = oracle_lib
@@ -518,6 +543,12 @@ def _pins_pass(o, mutation):
                         o.mnorm2(lp, w, eta, -1.0, z1[0] - z2[0], z1[1] - z2[1]) * (1 + 1e-12) + 1e-12:
                     return False
         o.set_mutation(0)
+        # the Halpern trajectory on a translation, with the mutation planted
+        r = o.solve(_translation_lp(), lpgen.base_specs(1), tol=1e-12, max_iter=7, check_every=1,
+                    detect_infeasibility=0, beta_s=0.0, beta_n=0.0, beta_a=1e9, warm_x=[0.5],
+                    warm_y=np.zeros(0), mutation=mutation)
+        if abs(r.x[0][0] - (0.5 - 7 * 0.998e-3)) > 1e-14:
+            return False
         # HiGHS on two random LPs, through the solver with the mutation planted
         for seed in (1, 2):
             lp = lpgen.random_lp(seed, 5, 7)
