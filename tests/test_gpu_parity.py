@@ -394,6 +394,17 @@ def test_halpern_trajectory_closed_form(lpb, precision):
         # FP32 iterates round once per step (at most about 6e-8 each); a wrong
         # Halpern weight, anchor or reflection is off by about delta per step
         assert x[0] == pytest.approx(0.5 - K * 0.998e-3, abs=1e-12 if precision == "fp64" else 1e-4)
+    # the dual side: x fixed at 0, one row x >= 1 (infeasible; detection off),
+    # c = 0 so w = 1 and sigma = 0.998; the dual operator is y -> y - sigma
+    lp = lpgen.from_dense(np.ones((1, 1)), [0.0], [1.0], [np.inf], [0.0], [0.0])
+    h = lpb.Handle(lp, precision=prec, check_every=1, detect_infeasibility=0, beta_s=0.0, beta_n=0.0,
+                   beta_a=1e9, fp64_polish=0)
+    for K in (1, 2, 7, 50):
+        b = h.solve(lpgen.base_specs(1), tol=1e-12, max_iter=K, warm_x=np.array([0.0]), warm_y=np.array([-0.25]))
+        r, x, y = b.result(0)
+        assert r.status == lpb.ITERATION_LIMIT and r.iters == K and r.restarts == 0
+        assert x[0] == 0.0
+        assert y[0] == pytest.approx(-0.25 - K * 0.998, abs=1e-10 if precision == "fp64" else 1e-3)
 
 
 def test_box_lp_without_rows(lpb):

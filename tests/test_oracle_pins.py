@@ -232,6 +232,17 @@ def test_halpern_trajectory_closed_form(oracle_lib):
                              warm_x=[0.5], warm_y=np.zeros(0))
         assert r.status[0] == 3 and r.iters[0] == K and r.restarts[0] == 0
         assert r.x[0][0] == pytest.approx(0.5 - K * delta, abs=1e-14)
+    # the dual side: x fixed at 0, one row x >= 1 (infeasible; detection off),
+    # c = 0 so w = 1 and sigma = eta = 0.998; the dual operator is the
+    # translation y -> y - sigma, so the K-th evaluated y is y^0 - K sigma
+    lp = lpgen.from_dense(np.ones((1, 1)), [0.0], [1.0], [np.inf], [0.0], [0.0])
+    for K in (1, 2, 7, 50):
+        r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-12, max_iter=K, check_every=1,
+                             detect_infeasibility=0, beta_s=0.0, beta_n=0.0, beta_a=1e9,
+                             warm_x=[0.0], warm_y=[-0.25])
+        assert r.status[0] == 3 and r.iters[0] == K and r.restarts[0] == 0
+        assert r.x[0][0] == 0.0
+        assert r.y[0][0] == pytest.approx(-0.25 - K * 0.998, abs=1e-12)
 
 
 def test_fixed_point_residual_zero_at_optimum(oracle_lib):
@@ -548,6 +559,11 @@ def _pins_pass(o, mutation):
                     detect_infeasibility=0, beta_s=0.0, beta_n=0.0, beta_a=1e9, warm_x=[0.5],
                     warm_y=np.zeros(0), mutation=mutation)
         if abs(r.x[0][0] - (0.5 - 7 * 0.998e-3)) > 1e-14:
+            return False
+        r = o.solve(lpgen.from_dense(np.ones((1, 1)), [0.0], [1.0], [np.inf], [0.0], [0.0]), lpgen.base_specs(1),
+                    tol=1e-12, max_iter=7, check_every=1, detect_infeasibility=0, beta_s=0.0, beta_n=0.0,
+                    beta_a=1e9, warm_x=[0.0], warm_y=[-0.25], mutation=mutation)
+        if abs(r.y[0][0] - (-0.25 - 7 * 0.998)) > 1e-12:
             return False
         # HiGHS on two random LPs, through the solver with the mutation planted
         for seed in (1, 2):
