@@ -245,6 +245,28 @@ def test_halpern_trajectory_closed_form(oracle_lib):
         assert r.y[0][0] == pytest.approx(-0.25 - K * 0.998, abs=1e-12)
 
 
+def test_restart_schedule_by_hand(oracle_lib):
+    """Sec. 4 "Restarts" in reading R5, on the translation LP, whose fixed-point
+    residual is the same at every check, so conditions (i) and (ii) fire only
+    when their beta is 1.  Checks every 4 iterations, 72 iterations; a check
+    at global index K (0-based) with inner index k restarts when k > beta_a K,
+    then k = 0, else k + 1; the last check ends the solve without a restart.
+    - beta_a = 0.36, beta_s = beta_n = 0: the checks at K = 3, 7, 11, ... see
+      k = 3 (> 1.08, restart), 3 (> 2.52, restart), 3 (< 3.96), 7 (> 5.4,
+      restart), 3, 7, 11 (> 9.72, restart), 3, 7, 11, 15, 19 (> 16.92,
+      restart), 3, 7, 11, 15, 19, 23 (K = 71, last): 5 restarts.
+    - beta_s = 1: every check but the last restarts: 18 checks, 17 restarts.
+    Restarting a translation at T(z) continues the same line, so the point is
+    still z^0 - K delta."""
+    lp = _translation_lp()
+    for kw, want in ((dict(beta_s=0.0, beta_n=0.0, beta_a=0.36), 5), (dict(beta_s=1.0, beta_n=0.0, beta_a=1e9), 17)):
+        r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-12, max_iter=72, check_every=4, detect_infeasibility=0,
+                             warm_x=[0.5], warm_y=np.zeros(0), **kw)
+        assert r.status[0] == 3 and r.iters[0] == 72
+        assert r.restarts[0] == want, kw
+        assert r.x[0][0] == pytest.approx(0.5 - 72 * 0.998e-3, abs=1e-14)
+
+
 def test_fixed_point_residual_zero_at_optimum(oracle_lib):
     """At a primal-dual optimum z*, T(z*) = z* (hand LP of the KKT golden)."""
     o = oracle_lib
