@@ -83,7 +83,7 @@ typedef struct {
     double eps_infeas;           /* < 0: use tol (reading R10) */
     int32_t threads;
     int32_t detect_infeasibility;
-    int32_t mutation;            /* 0; a test sets 1..8 to plant one known mistake */
+    int32_t mutation;            /* 0; a test sets 1..9 to plant one known mistake */
     int32_t reduced_cost;        /* 0: Pi_B as printed; 1: robust to large bounds (R19) */
 } orc_options;
 
@@ -124,7 +124,8 @@ void orc_default_options(orc_options* o) {
  *  3 Halpern anchor term dropped 4 reduced cost left out of the dual residual
  *  5 c scaled by 1/D_c           6 support function with a and b swapped
  *  7 M-norm diagonal weights swapped
- *  8 robust reduced cost paired with the wrong bound                          */
+ *  8 robust reduced cost paired with the wrong bound
+ *  9 primal-weight ratio inverted (||dx|| / ||dy||, as printed)              */
 static int32_t g_mutation = 0;
 void orc_set_mutation(int32_t k) { g_mutation = k; }
 
@@ -651,7 +652,7 @@ static void run_group(const shared_data* sd, lp_state* st, int32_t cnt, double t
                 double ddx = 0.0, ddy = 0.0;
                 for (int32_t q = 0; q < n; ++q) { double t = ax_[q] - s->x0[q]; ddx += t * t; }
                 for (int32_t q = 0; q < m; ++q) { double t = ay_[q] - s->y0[q]; ddy += t * t; }
-                double d = sqrt(ddy) / sqrt(ddx);
+                double d = g_mutation == 9 ? sqrt(ddx) / sqrt(ddy) : sqrt(ddy) / sqrt(ddx);
                 if (ddx > 0.0 && ddy > 0.0 && isfinite(d) && d > 0.0) {
                     s->w = exp(o->theta * log(d) + (1.0 - o->theta) * log(s->w));
                     s->tau = sd->eta / s->w;

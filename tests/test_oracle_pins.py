@@ -267,6 +267,31 @@ def test_restart_schedule_by_hand(oracle_lib):
         assert r.x[0][0] == pytest.approx(0.5 - 72 * 0.998e-3, abs=1e-14)
 
 
+def test_primal_weight_update_by_hand(oracle_lib):
+    """Sec. 4 "Step-size and primal weight" in readings R3 and R6/R7, by hand.
+    x1 moves freely with cost 0.3; x2 is fixed at 0 under the row x2 >= 2
+    (infeasible, detection off); x3 is fixed at 0 with cost 0.4.  A = [0 1 0]
+    needs no scaling and ||A|| = 1, so eta = 0.998; w0 = ||c|| / ||b|| =
+    0.5 / 2.  From z0 = 0 the first step gives dx = -tau0 c1 (x1 only) and
+    dy = -2 sigma0 (y^ = sigma (v - Pi(v)) with v = 0, Pi(v) = 2).  beta_s = 1
+    restarts at that first check: d = ||dy|| / ||dx|| = 2 w0^2 / c1 and
+    w1 = exp(theta log d + (1 - theta) log w0) with theta = 1/2.  The second
+    and last iteration steps from the new anchor with tau1 = eta / w1,
+    sigma1 = eta w1, so x1 = -c1 (tau0 + tau1) and y = -2 (sigma0 + sigma1).
+    The printed ratio ||dx|| / ||dy|| would give x1 = -1.584 instead of -2.125."""
+    lp = lpgen.from_dense(np.array([[0.0, 1.0, 0.0]]), [0.3, 0.0, 0.4], [2.0], [INF], [-1e6, 0.0, 0.0],
+                          [1e6, 0.0, 0.0])
+    eta, c1, w0 = 0.998, 0.3, 0.25
+    d = 2 * w0 ** 2 / c1
+    w1 = math.exp(0.5 * math.log(d) + 0.5 * math.log(w0))
+    r = oracle_lib.solve(lp, lpgen.base_specs(1), tol=1e-12, max_iter=2, check_every=1, detect_infeasibility=0,
+                         beta_s=1.0, beta_n=0.0, beta_a=1e9, warm_x=[0.0, 0.0, 0.0], warm_y=[0.0])
+    assert r.eta == pytest.approx(eta, rel=1e-12)
+    assert r.status[0] == 3 and r.iters[0] == 2 and r.restarts[0] == 1
+    assert r.x[0][0] == pytest.approx(-c1 * (eta / w0 + eta / w1), rel=1e-12)
+    assert r.y[0][0] == pytest.approx(-2 * (eta * w0 + eta * w1), rel=1e-12)
+
+
 def test_fixed_point_residual_zero_at_optimum(oracle_lib):
     """At a primal-dual optimum z*, T(z*) = z* (hand LP of the KKT golden)."""
     o = oracle_lib
@@ -587,6 +612,14 @@ def _pins_pass(o, mutation):
                     beta_a=1e9, warm_x=[0.0], warm_y=[-0.25], mutation=mutation)
         if abs(r.y[0][0] - (-0.25 - 7 * 0.998)) > 1e-12:
             return False
+        # the primal-weight update by hand, with the mutation planted
+        lpw = lpgen.from_dense(np.array([[0.0, 1.0, 0.0]]), [0.3, 0.0, 0.4], [2.0], [INF], [-1e6, 0.0, 0.0],
+                               [1e6, 0.0, 0.0])
+        r = o.solve(lpw, lpgen.base_specs(1), tol=1e-12, max_iter=2, check_every=1, detect_infeasibility=0,
+                    beta_s=1.0, beta_n=0.0, beta_a=1e9, warm_x=[0.0, 0.0, 0.0], warm_y=[0.0], mutation=mutation)
+        w1 = math.sqrt((2 * 0.25 ** 2 / 0.3) * 0.25)
+        if abs(r.x[0][0] + 0.3 * (0.998 / 0.25 + 0.998 / w1)) > 1e-9:
+            return False
         # HiGHS on two random LPs, through the solver with the mutation planted
         for seed in (1, 2):
             lp = lpgen.random_lp(seed, 5, 7)
@@ -604,6 +637,6 @@ def test_pins_pass_without_mutation(oracle_lib):
     assert _pins_pass(oracle_lib, 0)
 
 
-@pytest.mark.parametrize("mutation", range(1, 9))
+@pytest.mark.parametrize("mutation", range(1, 10))
 def test_planted_mistakes_are_caught(oracle_lib, mutation):
     assert not _pins_pass(oracle_lib, mutation)
