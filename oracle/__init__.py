@@ -77,6 +77,14 @@ def lib():
         _lib.orc_solve.restype = i32
         _lib.orc_solve.argtypes = [C.POINTER(_Problem), i32, vp, vp, vp, vp, vp, d, i64,
                                    C.POINTER(Options), vp, vp, vp, vp, C.POINTER(_Result), C.POINTER(d)]
+        _lib.orc_prepare.restype = vp
+        _lib.orc_prepare.argtypes = [C.POINTER(_Problem), C.POINTER(Options)]
+        _lib.orc_prepared_eta.restype = d
+        _lib.orc_prepared_eta.argtypes = [vp]
+        _lib.orc_prepared_free.argtypes = [vp]
+        _lib.orc_solve_prepared.restype = i32
+        _lib.orc_solve_prepared.argtypes = [vp, i32, vp, vp, vp, vp, vp, d, i64, C.POINTER(Options), vp, vp, vp,
+                                            vp, C.POINTER(_Result)]
         for f in ("orc_project_box", "orc_project_barrier", "orc_project_recession"):
             getattr(_lib, f).argtypes = [i32, vp, vp, vp, vp]
         _lib.orc_support.restype = d
@@ -137,12 +145,7 @@ class SolveResult:
     eta: float
 
 
-def solve(lp, specs, tol: float = 1e-4, max_iter: int = 100000, options: Options | None = None,
-          warm_x=None, warm_y=None, want_xy: bool = True, **kw) -> SolveResult:
-    """Batched restarted reflected-Halpern PDHG (Sec. 4-5) on the CPU in FP64."""
-    o = options if options is not None else default_options(**kw)
-    h = _Held(lp)
-    q = len(specs)
+def _spec_arrays(specs, q, lp, warm_x, warm_y, want_xy):
     kind = np.ascontiguousarray(specs.kind, dtype=np.int32)
     var = np.ascontiguousarray(specs.var, dtype=np.int32)
     lo, hi, sg = _f64(specs.lo), _f64(specs.hi), _f64(specs.sign)
@@ -150,6 +153,23 @@ def solve(lp, specs, tol: float = 1e-4, max_iter: int = 100000, options: Options
     wy = None if warm_y is None else _f64(np.asarray(warm_y).reshape(q, lp.m))
     x = np.zeros((q, lp.n)) if want_xy else None
     y = np.zeros((q, lp.m)) if want_xy else None
+    return kind, var, lo, hi, sg, wx, wy, x, y
+
+
+def _result(res, q, x, y, eta):
+    g = lambda f, dt: np.array([getattr(res[i], f) for i in range(q)], dtype=dt)
+    return SolveResult(g("status", np.int32), g("obj", float), g("dual_obj", float),
+                       g("rel_primal", float), g("rel_dual", float), g("rel_gap", float),
+                       g("iters", np.int64), g("restarts", np.int32), x, y, eta)
+
+
+def solve(lp, specs, tol: float = 1e-4, max_iter: int = 100000, options: Options | None = None,
+          warm_x=None, warm_y=None, want_xy: bool = True, **kw) -> SolveResult:
+    """Batched restarted reflected-Halpern PDHG (Sec. 4-5) on the CPU in FP64."""
+    o = options if options is not None else default_options(**kw)
+    h = _Held(lp)
+    q = len(specs)
+    kind, var, lo, hi, sg, wx, wy, x, y = _spec_arrays(specs, q, lp, warm_x, warm_y, want_xy)
     res = (_Result * max(q, 1))()
     eta = C.c_double(0.0)
     rc = lib().orc_solve(C.byref(h.p), q, _ptr(kind), _ptr(var), _ptr(lo), _ptr(hi), _ptr(sg), tol,
@@ -157,10 +177,50 @@ def solve(lp, specs, tol: float = 1e-4, max_iter: int = 100000, options: Options
                          C.byref(eta))
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc})")
-    g = lambda f, dt: np.array([getattr(res[i], f) for i in range(q)], dtype=dt)
-    return SolveResult(g("status", np.int32), g("obj", float), g("dual_obj", float),
-                       g("rel_primal", float), g("rel_dual", float), g("rel_gap", float),
-                       g("iters", np.int64), g("restarts", np.int32), x, y, eta.value)
+    return _result(res, q, x, y, eta.value)
+
+
+class Prepared:
+    """The per-matrix set-up of ``solve`` (scaling, scaled values, eta, ||b~||)
+    done once, for several solves on the same matrix.  ``solve`` on a
+    Prepared gives the same results as the module-level ``solve`` with the
+    same options; the set-up options are those given here."""
+
+    def __init__(self, lp, options: Options | None = None, **kw):
+        self.lp = lp
+        self.options = options if options is not None else default_options(**kw)
+        self._held = _Held(lp)
+        self._h = lib().orc_prepare(C.byref(self._held.p), C.byref(self.options))
+        if not self._h:
+            raise ValueError("oracle set-up failed")
+        self.eta = lib().orc_prepared_eta(self._h)
+
+    def solve(self, specs, tol: float = 1e-4, max_iter: int = 100000, warm_x=None, warm_y=None,
+              want_xy: bool = True, **kw) -> SolveResult:
+        o = Options.from_buffer_copy(self.options)
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise AttributeError(k)
+            setattr(o, k, v)
+        q = len(specs)
+        kind, var, lo, hi, sg, wx, wy, x, y = _spec_arrays(specs, q, self.lp, warm_x, warm_y, want_xy)
+        res = (_Result * max(q, 1))()
+        rc = lib().orc_solve_prepared(self._h, q, _ptr(kind), _ptr(var), _ptr(lo), _ptr(hi), _ptr(sg), tol,
+                                      int(max_iter), C.byref(o), _ptr(wx), _ptr(wy), _ptr(x), _ptr(y), res)
+        if rc != 0:
+            raise ValueError(f"oracle rejected the arguments (code {rc})")
+        return _result(res, q, x, y, self.eta)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_prepared_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kkt(lp, kind: int, var: int, lo: float, hi: float, sign: float, x, y, reduced_cost: int = 0) -> dict:

@@ -83,7 +83,7 @@ typedef struct {
     double eps_infeas;           /* < 0: use tol (reading R10) */
     int32_t threads;
     int32_t detect_infeasibility;
-    int32_t mutation;            /* 0; a test sets 1..9 to plant one known mistake */
+    int32_t mutation;            /* 0; a test sets 1..12 to plant one known mistake */
     int32_t reduced_cost;        /* 0: Pi_B as printed; 1: robust to large bounds (R19) */
 } orc_options;
 
@@ -312,8 +312,8 @@ void orc_scaling(const orc_problem* p, int32_t ruiz_iters, int32_t pock_chamboll
                 rs[i] += a;
                 cs[j] += a;
             }
-        for (int32_t i = 0; i < m; ++i) if (rs[i] > 0.0) D_r[i] /= sqrt(rs[i]);
-        for (int32_t j = 0; j < n; ++j) if (cs[j] > 0.0) D_c[j] /= sqrt(cs[j]);
+        for (int32_t i = 0; i < m; ++i) if (rs[i] > 0.0) D_r[i] /= g_mutation == 12 ? rs[i] : sqrt(rs[i]);
+        for (int32_t j = 0; j < n; ++j) if (cs[j] > 0.0) D_c[j] /= g_mutation == 12 ? cs[j] : sqrt(cs[j]);
     }
     free(rs); free(cs);
 }
@@ -637,10 +637,11 @@ static void run_group(const shared_data* sd, lp_state* st, int32_t cnt, double t
         if (nact == 0) break;
         if (K + 1 == max_iter) break;
         /* Sec. 5 "Restarts": averaged residual over the LPs still active (R11) */
-        double rt = rsum / (double)nact;
+        double rt = rsum / (double)(g_mutation == 11 ? cnt : nact);
         if (r0 < 0.0) { r0 = rt; r_prev = rt; }
+        int no_progress = g_mutation == 10 ? rt < r_prev : rt > r_prev;
         int restart = (rt <= o->beta_s * r0) ||                       /* sufficient decay */
-                      (rt <= o->beta_n * r0 && rt > r_prev) ||         /* necessary decay, no progress */
+                      (rt <= o->beta_n * r0 && no_progress) ||         /* necessary decay, no progress */
                       ((double)k > o->beta_a * (double)K);             /* artificial: k > beta_a K */
         if (restart) {
             for (int32_t j = 0; j < cnt; ++j) {
@@ -681,50 +682,88 @@ static void run_group(const shared_data* sd, lp_state* st, int32_t cnt, double t
         if (st[j].active) finish(sd, &st[j], ORC_ITERATION_LIMIT, max_iter, x_out, y_out, res);
 }
 
-/* Solve `num_lps` LPs sharing A.  Override record q: kind[q], var[q], lo[q],
- * hi[q], sign[q].  warm_x (n x num_lps, column q = LP q) and warm_y may be
- * NULL.  x_out / y_out (n x num_lps, m x num_lps) may be NULL.  Returns 0, or
- * a negative code for invalid arguments.                                   */
-int32_t orc_solve(const orc_problem* p, int32_t num_lps, const int32_t* kind, const int32_t* var,
-                  const double* lo, const double* hi, const double* sign, double tol, int64_t max_iter,
-                  const orc_options* o, const double* warm_x, const double* warm_y, double* x_out,
-                  double* y_out, orc_result* res, double* eta_out) {
-    if (!p || !o || num_lps < 0 || max_iter < 1 || !(tol > 0.0) || o->check_every < 1) return -1;
+/* ------------------------------------------------------------------------ */
+/* Per-matrix set-up, done once and shared by any number of solves: the      */
+/* scaling factors (R1), the scaled values A~ and row bounds, eta (Sec. 4    */
+/* "Step-size", R2) and ||b~|| (R3).  The problem's arrays are referenced,   */
+/* not copied: they must outlive the prepared object.                       */
+/* ------------------------------------------------------------------------ */
+struct orc_prepared {
+    orc_problem p;            /* the caller's arrays */
+    shared_data sd;
+    double* Dr;
+    double* Dc;
+    double bn;                /* ||b~|| (R3) */
+};
+typedef struct orc_prepared orc_prepared;
+
+orc_prepared* orc_prepare(const orc_problem* p, const orc_options* o) {
+    if (!p || !o) return NULL;
     g_mutation = o->mutation;
     int32_t m = p->m, n = p->n;
-    shared_data sd;
-    memset(&sd, 0, sizeof(sd));
-    sd.p = p;
-    sd.rc_mode = o->reduced_cost ? 1 : 0;
-    double* Dr = dvec(m);
-    double* Dc = dvec(n);
-    orc_scaling(p, o->ruiz_iters, o->pock_chambolle, Dr, Dc);
-    sd.Dr = Dr;
-    sd.Dc = Dc;
-    sd.svals = dvec(p->nnz);
+    orc_prepared* h = (orc_prepared*)calloc(1, sizeof(orc_prepared));
+    h->p = *p;
+    shared_data* sd = &h->sd;
+    sd->p = &h->p;
+    h->Dr = dvec(m);
+    h->Dc = dvec(n);
+    orc_scaling(p, o->ruiz_iters, o->pock_chambolle, h->Dr, h->Dc);
+    sd->Dr = h->Dr;
+    sd->Dc = h->Dc;
+    sd->svals = dvec(p->nnz);
     for (int32_t i = 0; i < m; ++i)
         for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
-            sd.svals[e] = Dr[i] * p->vals[e] * Dc[p->col_idx[e]];
-    sd.ps = *p;
-    sd.ps.vals = sd.svals;
-    sd.lts = dvec(m);
-    sd.uts = dvec(m);
-    for (int32_t i = 0; i < m; ++i) { sd.lts[i] = Dr[i] * p->row_lo[i]; sd.uts[i] = Dr[i] * p->row_hi[i]; }
+            sd->svals[e] = h->Dr[i] * p->vals[e] * h->Dc[p->col_idx[e]];
+    sd->ps = *p;
+    sd->ps.vals = sd->svals;
+    sd->lts = dvec(m);
+    sd->uts = dvec(m);
+    for (int32_t i = 0; i < m; ++i) { sd->lts[i] = h->Dr[i] * p->row_lo[i]; sd->uts[i] = h->Dr[i] * p->row_hi[i]; }
     /* Sec. 4 "Step-size": eta = 0.998 / ||A~||_2 (R2) */
-    double nrm = orc_norm2_estimate(m, n, p->row_ptr, p->col_idx, sd.svals, o->power_max_iter,
+    double nrm = orc_norm2_estimate(m, n, p->row_ptr, p->col_idx, sd->svals, o->power_max_iter,
                                     o->power_tol, o->power_seed, NULL);
-    sd.eta = 0.998 / (nrm > 0.0 ? nrm : 1.0);
-    if (eta_out) *eta_out = sd.eta;
+    sd->eta = 0.998 / (nrm > 0.0 ? nrm : 1.0);
     /* R3: ||b~||, b~_i = the finite row bound of larger magnitude */
     double b2 = 0.0;
     for (int32_t i = 0; i < m; ++i) {
-        double l = sd.lts[i], u = sd.uts[i], b = 0.0;
+        double l = sd->lts[i], u = sd->uts[i], b = 0.0;
         if (isfinite(l) && isfinite(u)) b = fabs(l) > fabs(u) ? l : u;
         else if (isfinite(l)) b = l;
         else if (isfinite(u)) b = u;
         b2 += b * b;
     }
-    double bn = sqrt(b2);
+    h->bn = sqrt(b2);
+    g_mutation = 0;
+    return h;
+}
+
+double orc_prepared_eta(const orc_prepared* h) { return h ? h->sd.eta : 0.0; }
+
+void orc_prepared_free(orc_prepared* h) {
+    if (!h) return;
+    free(h->Dr); free(h->Dc); free(h->sd.svals); free(h->sd.lts); free(h->sd.uts);
+    free(h);
+}
+
+/* Solve `num_lps` LPs on a prepared matrix.  Override record q: kind[q],
+ * var[q], lo[q], hi[q], sign[q].  warm_x (n x num_lps, column q = LP q) and
+ * warm_y may be NULL.  x_out / y_out (n x num_lps, m x num_lps) may be NULL.
+ * The set-up options of `o` (scaling, power iteration) are those the matrix
+ * was prepared with; the rest apply to this solve.  Returns 0, or a negative
+ * code for invalid arguments.                                              */
+int32_t orc_solve_prepared(const orc_prepared* h, int32_t num_lps, const int32_t* kind, const int32_t* var,
+                           const double* lo, const double* hi, const double* sign, double tol, int64_t max_iter,
+                           const orc_options* o, const double* warm_x, const double* warm_y, double* x_out,
+                           double* y_out, orc_result* res) {
+    if (!h || !o || num_lps < 0 || max_iter < 1 || !(tol > 0.0) || o->check_every < 1) return -1;
+    g_mutation = o->mutation;
+    const orc_problem* p = &h->p;
+    int32_t m = p->m, n = p->n;
+    shared_data sd = h->sd;
+    sd.rc_mode = o->reduced_cost ? 1 : 0;
+    const double* Dr = h->Dr;
+    const double* Dc = h->Dc;
+    const double bn = h->bn;
 
     lp_state* st = (lp_state*)calloc((size_t)(num_lps > 0 ? num_lps : 1), sizeof(lp_state));
     for (int32_t q = 0; q < num_lps; ++q) {
@@ -771,7 +810,21 @@ int32_t orc_solve(const orc_problem* p, int32_t num_lps, const int32_t* kind, co
     }
     for (int32_t q = 0; q < num_lps; ++q) lp_free(&st[q]);
     free(st);
-    free(Dr); free(Dc); free(sd.svals); free(sd.lts); free(sd.uts);
     g_mutation = 0;
     return 0;
+}
+
+/* Solve `num_lps` LPs sharing A: set-up, solve, release (see
+ * orc_solve_prepared for the arguments).                                   */
+int32_t orc_solve(const orc_problem* p, int32_t num_lps, const int32_t* kind, const int32_t* var,
+                  const double* lo, const double* hi, const double* sign, double tol, int64_t max_iter,
+                  const orc_options* o, const double* warm_x, const double* warm_y, double* x_out,
+                  double* y_out, orc_result* res, double* eta_out) {
+    if (!p || !o || num_lps < 0 || max_iter < 1 || !(tol > 0.0) || o->check_every < 1) return -1;
+    orc_prepared* h = orc_prepare(p, o);
+    if (eta_out) *eta_out = orc_prepared_eta(h);
+    int32_t rc = orc_solve_prepared(h, num_lps, kind, var, lo, hi, sign, tol, max_iter, o, warm_x, warm_y,
+                                    x_out, y_out, res);
+    orc_prepared_free(h);
+    return rc;
 }

@@ -420,7 +420,7 @@ lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_
     } else {
         // one CUDA graph per interval shape, replayed while the shape holds;
         // a new shape updates the executable graph in place when it can
-        const GraphKey key{ln.ncol, uni, L, stall_checks, h->ws_epoch, (int)(sizeof(T))};
+        const GraphKey key = interval_key(h, ln, L, stall_checks, uni, (int)sizeof(T));
         if (!ln.exec || !(ln.gkey == key)) {
             cudaGraph_t g = nullptr;
             LPB_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

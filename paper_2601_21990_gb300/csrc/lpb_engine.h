@@ -27,12 +27,27 @@ namespace lpb {
 
 enum LanePrec { kPrecF32 = 0, kPrecF64 = 1, kPrecDfl = 2 };
 
-// what an interval's captured graph depends on besides the lane's buffers
+// Everything an interval's captured graph bakes into its kernel and copy
+// nodes: the shape (active columns, the single group if there is one,
+// interval length, stall setting, iterate size), the lane's leading dimension
+// and buffers (identified by their base addresses), the check workspace
+// generation, and each matrix's long-row list and launch shape.  A replay is
+// valid only while every field holds; any difference re-captures.
 struct GraphKey {
     int ncol = -1, uni = -1, L = -1, stall = -1, ws_epoch = -1, tsize = 0;
+    int ld = -1;
+    const void* X = nullptr;            // lane iterate blocks (all allocated together)
+    const void* Y = nullptr;
+    const void* rec = nullptr;          // per-column records and their pinned mirror
+    const void* rec_h = nullptr;
+    const int* long_a = nullptr;        // long-row lists of A~ and A~^T
+    const int* long_at = nullptr;
+    int n_long_a = -1, n_long_at = -1, thr_a = -1, thr_at = -1, shift_a = -1, shift_at = -1;
     bool operator==(const GraphKey& o) const {
         return ncol == o.ncol && uni == o.uni && L == o.L && stall == o.stall && ws_epoch == o.ws_epoch &&
-               tsize == o.tsize;
+               tsize == o.tsize && ld == o.ld && X == o.X && Y == o.Y && rec == o.rec && rec_h == o.rec_h &&
+               long_a == o.long_a && long_at == o.long_at && n_long_a == o.n_long_a && n_long_at == o.n_long_at &&
+               thr_a == o.thr_a && thr_at == o.thr_at && shift_a == o.shift_a && shift_at == o.shift_at;
     }
 };
 
@@ -183,5 +198,30 @@ lpb_err lane_migrate(lpb_ctx* h, Lane& src, Lane& dst, GroupRun& g, int id_dst, 
 void add_interval_times(lpb_ctx* h, int L, lpb_profile* prof);
 
 double step_bytes(int prec, int nnz, int m, int n, bool primal, bool check, int ncol);
+
+// The key of an interval of L iterations on lane ln (see GraphKey).
+inline GraphKey interval_key(const lpb_ctx* h, const Lane& ln, int L, int stall_checks, int uni, int tsize) {
+    GraphKey k;
+    k.ncol = ln.ncol;
+    k.uni = uni;
+    k.L = L;
+    k.stall = stall_checks;
+    k.ws_epoch = h->ws_epoch;
+    k.tsize = tsize;
+    k.ld = ln.cap;
+    k.X = ln.X;
+    k.Y = ln.Y;
+    k.rec = ln.rec;
+    k.rec_h = ln.rec_h;
+    k.long_a = h->A.long_rows;
+    k.long_at = h->At.long_rows;
+    k.n_long_a = h->A.n_long;
+    k.n_long_at = h->At.n_long;
+    k.thr_a = h->A.long_thr;
+    k.thr_at = h->At.long_thr;
+    k.shift_a = h->A.g_shift;
+    k.shift_at = h->At.g_shift;
+    return k;
+}
 
 }  // namespace lpb

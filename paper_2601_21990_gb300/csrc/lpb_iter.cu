@@ -27,6 +27,8 @@
 // weights come from a table written by the check kernels.  The kernels are
 // instantiated for float (mixed path), double (FP64 path) and dfloat (the
 // mixed path's polish phase: double-float values on the FP32 pipe).
+#include <atomic>
+
 #include "lpb_internal.h"
 
 // resident blocks per SM the step kernels are compiled for (register cap)
@@ -425,20 +427,35 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::v) k_step(const StepArgs
     }
 }
 
+// Launch shapes are cached per device: SM count and resident blocks per SM
+// packed into one int (sms * 64 + per_sm, 0 = not yet looked up), published
+// with release / acquire so that every thread (the server runs one worker per
+// matrix) reads both values of one lookup or does the lookup itself.
+constexpr int kShapeDevices = 64;
+inline int pack_shape(int sms, int per_sm) {
+    sms = sms > 0 ? sms : 1;
+    per_sm = per_sm > 0 ? (per_sm < 63 ? per_sm : 63) : 1;
+    return sms * 64 + per_sm;
+}
+
 template <typename T, int G, bool CHECK, bool PRIMAL>
 cudaError_t launch_k(const StepArgs<T>& a, cudaStream_t s) {
     constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
-    // resident blocks per SM and SM count, looked up once per instantiation
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-        int dev = 0, b = 0, n = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<T, G, CHECK, PRIMAL>, kBlock, 0) != cudaSuccess)
-            return cudaGetLastError();
-        sms = n > 0 ? n : 1;
-        per_sm = b > 0 ? b : 1;
+    static std::atomic<int> shape[kShapeDevices];  // static storage: starts at 0
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int packed = dev >= 0 && dev < kShapeDevices ? shape[dev].load(std::memory_order_acquire) : 0;
+    if (packed == 0) {
+        int b = 0, n = 0;
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<T, G, CHECK, PRIMAL>, kBlock, 0)) !=
+            cudaSuccess)
+            return e;
+        packed = pack_shape(n, b);
+        if (dev >= 0 && dev < kShapeDevices) shape[dev].store(packed, std::memory_order_release);
     }
+    const int sms = packed / 64, per_sm = packed % 64;
     const int need = (a.rows + GPB - 1) / GPB;
     const int persist = need < sms * per_sm ? need : sms * per_sm;
     dim3 grid(a.n_long + persist, (a.ncol + TN - 1) / TN);

@@ -20,3 +20,18 @@ def test_double_float_helpers(tmp_path):
                            os.path.join(ROOT, "tests", "native", "df_host_test.cu"), "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout[-2000:]
+
+
+def test_graph_key_changes_with_every_baked_input(tmp_path):
+    """A captured interval graph is replayed only while its key holds; the key
+    must change with every pointer, size and launch shape the graph bakes in
+    (lane buffers and leading dimension, check workspace, long-row lists)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "graph_key_test"
+    subprocess.check_call([nvcc, "-O1", "-std=c++17", "-I", os.path.join(ROOT, "paper_2601_21990_gb300", "csrc"),
+                           "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "native", "graph_key_test.cu"), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout[-2000:]

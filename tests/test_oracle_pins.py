@@ -14,6 +14,7 @@ import os
 import numpy as np
 import pytest
 
+import handcases
 import lpgen
 
 INF = np.inf
@@ -166,6 +167,18 @@ def test_ruiz_diagonal_closed_form(oracle_lib):
     np.testing.assert_allclose(dr2 * d * dc2, np.ones(3), rtol=1e-15)
 
 
+def test_pock_chambolle_pass_by_hand(oracle_lib):
+    """Reading R1: one Pock-Chambolle pass (alpha = 1) divides each row and
+    column by the square root of its absolute sum, both sums taken from the
+    same matrix; alone and after one Ruiz pass, on a 2 x 2 matrix with the
+    factors written out by hand (tests/handcases.py)."""
+    for a, ruiz, dr_want, dc_want in handcases.pc_cases():
+        lp = lpgen.from_dense(a, [1.0, 1.0], [-1.0, -1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0])
+        dr, dc = oracle_lib.scaling(lp, ruiz_iters=ruiz, pock_chambolle=True)
+        np.testing.assert_allclose(dr, dr_want, rtol=1e-14)
+        np.testing.assert_allclose(dc, dc_want, rtol=1e-14)
+
+
 def test_ruiz_fixed_point_unit_inf_norms(oracle_lib):
     lp = lpgen.random_lp(3, 15, 11, density=0.5)
     dr, dc = oracle_lib.scaling(lp, ruiz_iters=60, pock_chambolle=False)
@@ -265,6 +278,28 @@ def test_restart_schedule_by_hand(oracle_lib):
         assert r.status[0] == 3 and r.iters[0] == 72
         assert r.restarts[0] == want, kw
         assert r.x[0][0] == pytest.approx(0.5 - 72 * 0.998e-3, abs=1e-14)
+
+
+def _restart_batch_solve(o, beta_n, mutation=0):
+    lp, specs, wx, wy = handcases.restart_batch()
+    return o.solve(lp, specs, tol=1e-12, max_iter=handcases.RESTART_BATCH_MAX_ITER, lockstep=1, warm_x=wx,
+                   warm_y=wy, beta_n=beta_n, mutation=mutation, **handcases.RESTART_BATCH_KW)
+
+
+def test_restart_conditions_and_active_mean_by_hand(oracle_lib):
+    """Sec. 4 "Restarts" condition (ii) and Sec. 5's batch-averaged residual
+    over the LPs still active (reading R11), on the five-LP lockstep batch of
+    tests/handcases.py: the mean residual falls at check 2 and rises at
+    check 3 while below beta_n r0, so condition (ii) restarts at check 3 for
+    beta_n = 0.9 and nothing restarts for beta_n = 0.5.  The statuses,
+    finishing iterations and optimal points are derived by hand as well."""
+    for beta_n, want in handcases.RESTART_BATCH_RESTARTS.items():
+        r = _restart_batch_solve(oracle_lib, beta_n)
+        assert r.status.tolist() == handcases.RESTART_BATCH_STATUS
+        assert r.iters.tolist() == handcases.RESTART_BATCH_ITERS
+        assert r.restarts.tolist() == want, beta_n
+        for q, xq in handcases.RESTART_BATCH_OPT_X.items():
+            np.testing.assert_allclose(r.x[q], xq, atol=1e-15)
 
 
 def test_primal_weight_update_by_hand(oracle_lib):
@@ -620,6 +655,18 @@ def _pins_pass(o, mutation):
         w1 = math.sqrt((2 * 0.25 ** 2 / 0.3) * 0.25)
         if abs(r.x[0][0] + 0.3 * (0.998 / 0.25 + 0.998 / w1)) > 1e-9:
             return False
+        # one Pock-Chambolle pass by hand, with the mutation planted
+        o.set_mutation(mutation)
+        for a, ruiz, dr_want, dc_want in handcases.pc_cases():
+            lp = lpgen.from_dense(a, [1.0, 1.0], [-1.0, -1.0], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0])
+            dr, dc = o.scaling(lp, ruiz_iters=ruiz, pock_chambolle=True)
+            if np.max(np.abs(dr - dr_want) / dr_want) > 1e-14 or np.max(np.abs(dc - dc_want) / dc_want) > 1e-14:
+                return False
+        o.set_mutation(0)
+        # restart condition (ii) and the mean over active LPs by hand
+        for beta_n, want in handcases.RESTART_BATCH_RESTARTS.items():
+            if _restart_batch_solve(o, beta_n, mutation).restarts.tolist() != want:
+                return False
         # HiGHS on two random LPs, through the solver with the mutation planted
         for seed in (1, 2):
             lp = lpgen.random_lp(seed, 5, 7)
@@ -637,6 +684,6 @@ def test_pins_pass_without_mutation(oracle_lib):
     assert _pins_pass(oracle_lib, 0)
 
 
-@pytest.mark.parametrize("mutation", range(1, 10))
+@pytest.mark.parametrize("mutation", range(1, 13))
 def test_planted_mistakes_are_caught(oracle_lib, mutation):
     assert not _pins_pass(oracle_lib, mutation)
