@@ -1,11 +1,14 @@
 """Benchmark: LPs solved per second by the batched PDHG solver on one GB300.
 
 A step is one complete batched solve (every LP of the batch to rel-KKT 1e-4,
-all hot-path steps: both fused SpMM steps, FP64 checks, restarts,
+all hot-path steps: both fused SpMM steps, the KKT checks, restarts,
 compaction) of a seeded synthetic batch whose matrix is already resident on
-the GPU.  The default workload is 64 strong-branching children of a shared
-A with m=20k, n=50k and power-law row lengths (nnz ~ 250k), FP32 iterates
-with FP64 checks.
+the GPU.  The default workload is the large strong-branching batch: 128
+children of a shared A with m=1M, n=2M, nnz ~10.5M (rows of 3-8 nonzeros
+plus 500 dense rows of 10k), FP32 iterates with double-float (about 48-bit)
+KKT and restart checks; its iterate blocks (1 GB per block) exceed L2 many
+times over.  The 1024-LP bound-tightening batch (m=n=100k, nnz=1M) is timed
+once more as an extra key.
 
 Prints ONE JSON line (rank 0).  Under torchrun with N>1 every rank solves
 its own, independently seeded batch (weak scaling, no collective on the data
@@ -37,13 +40,67 @@ UNIT = "LPs/s"
 TOL = 1e-4
 FALLBACK_HBM_GBS = 6800.0
 
-# cpu_lps: the oracle's default sample (0: a single oracle solve takes minutes)
+# cpu_lps: the oracle's default sample of whole solves; golden: the seeded
+# subset of a full-size batch whose oracle results (iterations to 1e-4 and
+# reference objectives) tests/golden/make_reference.py stores, for workloads
+# where one oracle solve takes minutes: there the oracle's sample is a bounded
+# number of iterations, scaled by its own iteration counts
 WORKLOADS = {
-    "sb_powerlaw": dict(fn=lambda seed: lpgen.sb_powerlaw(seed=seed), max_iter=100000, cpu_lps=64),
-    "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000, cpu_lps=16),
-    "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000, cpu_lps=0),
-    "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000, cpu_lps=0),
+    "sb_powerlaw": dict(fn=lambda seed: lpgen.sb_powerlaw(seed=seed), max_iter=100000, cpu_lps=64,
+                        golden="sb_powerlaw_seed0"),
+    "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000, cpu_lps=16, golden=None),
+    "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000, cpu_lps=0,
+                        golden="obbt_square_seed0_subset16"),
+    "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000, cpu_lps=0,
+                     golden="sb_large_seed0_subset16"),
 }
+DTYPE_MIXED = "f32-iterates/double-float-checks"
+# iterations of the oracle's bounded sample (per LP) where whole solves take minutes
+ORACLE_SAMPLE_ITERS = 64
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def golden_case(name):
+    """The oracle's stored results for `name`, or None when the file is
+    missing, lacks the case, or was written by another oracle source."""
+    if not name:
+        return None
+    try:
+        g = json.load(open(os.path.join(ROOT, "tests", "golden", "reference_objectives.json")))
+        src = open(os.path.join(ROOT, "oracle", "pdhg_oracle.c"), "rb").read()
+        if g.get("oracle_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return g["cases"].get(name)
+    except Exception:
+        return None
+
+
+def golden_lps_and_ref(name, q):
+    """(LP indices, oracle status at the solve tolerance, reference objective)
+    of the stored case: a seeded subset, or the whole batch."""
+    c = golden_case(name)
+    if c is None:
+        return None
+    if "lps" in c:
+        return list(c["lps"]), np.asarray(c["status"]), np.asarray(c["ref_obj"]), np.asarray(c["iters"])
+    return list(range(q)), np.asarray(c["status"]), np.asarray(c["obj"]), None
 
 
 def dist_env():
@@ -154,6 +211,35 @@ def ncu_traffic(kernel_name: str, workload: str):
     return ent.get("dram_bytes_per_launch"), f"ncu DRAM bytes of one {ent.get('ncol')}-LP launch: {ent.get('note')}"
 
 
+def oracle_scaled_sample(w, gold, cores, iters):
+    """The oracle on the stored subset for `iters` iterations per LP (OpenMP
+    over LPs, the set-up done once outside the timing): per LP-iteration core
+    time, and the wall time the subset's whole solve takes at that rate with
+    the oracle's own iteration counts to 1e-4 (the longest LP, or the total
+    over the cores, whichever is larger)."""
+    import oracle
+
+    oracle.build()
+    lps, status, _, need = gold
+    sp = w.specs.subset(lps)
+    t = time.perf_counter()
+    prep = oracle.Prepared(w.lp)
+    setup_s = time.perf_counter() - t
+    return prep, sp, setup_s, status, need
+
+
+def oracle_sample_rate(prep, sp, status, need, cores, iters):
+    s = len(sp)
+    t = time.perf_counter()
+    prep.solve(sp, tol=TOL, max_iter=iters, threads=cores, lockstep=0, want_xy=False)
+    dt = time.perf_counter() - t
+    par = max(1, min(cores, s))
+    per_lp_iter = dt * par / (iters * s)  # core-seconds of one LP-iteration
+    wall = max(float(np.max(need)), float(np.sum(need)) / par) * per_lp_iter
+    solved = int(np.sum(status <= 2))
+    return solved / wall, dt, wall
+
+
 def run_reference(args, rank, world):
     """The CPU oracle, as it stands, on the host cores: a bounded sample."""
     if world > 1 and rank != 0:
@@ -163,41 +249,78 @@ def run_reference(args, rank, world):
     oracle.build()
     w = WORKLOADS[args.workload]["fn"](args.seed)
     q = len(w.specs)
-    # a bounded sample per step: about 640 LP solves over the whole run
-    sample = min(q, args.ref_lps, max(4, 640 // max(args.steps, 1)))
-    sp = w.specs.subset(range(sample))
     cores = os.cpu_count() or 1
-    for _ in range(args.warmup if args.ref_warmup else 0):
-        oracle.solve(w.lp, sp, tol=TOL, max_iter=WORKLOADS[args.workload]["max_iter"], threads=cores,
-                     lockstep=0, want_xy=False)
-    times, nsolved = [], 0
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        r = oracle.solve(w.lp, sp, tol=TOL, max_iter=WORKLOADS[args.workload]["max_iter"], threads=cores,
-                         lockstep=0, want_xy=False)
-        times.append(time.perf_counter() - t)
-        nsolved += int(np.sum(r.status <= 2))
-    total = sum(times)
-    v = nsolved / total
-    desc = f"{sample} of {q} LPs of {w.name}, each solved alone (own restarts), OpenMP over LPs"
+    max_iter = WORKLOADS[args.workload]["max_iter"]
+    gold = golden_lps_and_ref(WORKLOADS[args.workload]["golden"], q)
+    if WORKLOADS[args.workload]["cpu_lps"] == 0:
+        if gold is None or gold[3] is None:
+            print(json.dumps({"impl": "reference", "unavailable": "one oracle solve of this workload takes minutes "
+                              "and the stored oracle iteration counts are missing or stale"}), flush=True)
+            return
+        prep, sp, setup_s, status, need = oracle_scaled_sample(w, gold, cores, ORACLE_SAMPLE_ITERS)
+        iters = max(4, ORACLE_SAMPLE_ITERS // 4)
+        for _ in range(args.warmup if args.ref_warmup else 0):
+            oracle_sample_rate(prep, sp, status, need, cores, iters)
+        times, walls = [], []
+        for _ in range(args.steps):
+            _, dt, wall = oracle_sample_rate(prep, sp, status, need, cores, iters)
+            times.append(dt)
+            walls.append(wall)
+        solved = int(np.sum(status <= 2))
+        v = solved / float(np.mean(walls))
+        desc = (f"{len(sp)} of {q} LPs of {w.name} (the stored seeded subset), each alone, OpenMP over LPs, "
+                f"{iters} iterations per LP per step; LPs/s = LPs the oracle solves at 1e-4 / the time its own "
+                f"iteration counts to 1e-4 take at the measured rate; set-up {setup_s:.1f} s once, not timed")
+        ms = 1e3 * float(np.mean(walls))
+        sample_lps = len(sp)
+    else:
+        # a bounded sample per step: about 640 LP solves over the whole run
+        sample = min(q, args.ref_lps, max(4, 640 // max(args.steps, 1)))
+        sp = w.specs.subset(range(sample))
+        prep = oracle.Prepared(w.lp)
+        for _ in range(args.warmup if args.ref_warmup else 0):
+            prep.solve(sp, tol=TOL, max_iter=max_iter, threads=cores, lockstep=0, want_xy=False)
+        times, nsolved = [], 0
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            r = prep.solve(sp, tol=TOL, max_iter=max_iter, threads=cores, lockstep=0, want_xy=False)
+            times.append(time.perf_counter() - t)
+            nsolved += int(np.sum(r.status <= 2))
+        total = sum(times)
+        v = nsolved / total
+        desc = f"{sample} of {q} LPs of {w.name}, each solved alone (own restarts), OpenMP over LPs"
+        ms = 1e3 * total / args.steps
+        sample_lps = sample
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "tol": TOL, "sample_lps": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "config": {"workload": w.name, "tol": TOL, "sample_lps": sample_lps},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(w, cores, budget_lps):
+def cpu_baseline(w, name, cores, budget_lps):
     import oracle
 
-    if budget_lps <= 0:
-        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": "none: one oracle solve of this workload takes minutes on the host cores"}
     oracle.build()
     q = len(w.specs)
+    if budget_lps <= 0:
+        gold = golden_lps_and_ref(WORKLOADS[name]["golden"], q)
+        if gold is None or gold[3] is None:
+            return {"value": None, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+                    "sample": "none: one oracle solve takes minutes and the stored iteration counts are missing"}
+        prep, sp, setup_s, status, need = oracle_scaled_sample(w, gold, cores, ORACLE_SAMPLE_ITERS)
+        v, dt, wall = oracle_sample_rate(prep, sp, status, need, cores, ORACLE_SAMPLE_ITERS)
+        prep.close()
+        return {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+                "sample": f"{len(sp)} of {q} LPs of {w.name} (the stored seeded subset), each alone, OpenMP over "
+                          f"LPs, {ORACLE_SAMPLE_ITERS} iterations per LP in {dt:.1f} s; LPs/s = LPs the oracle "
+                          f"solves at 1e-4 / the {wall:.0f} s its own iteration counts to 1e-4 "
+                          f"(max {int(np.max(need))}) take at that rate; set-up {setup_s:.1f} s, not counted",
+                "setup_s": setup_s}
     sample = min(q, budget_lps)
     sp = w.specs.subset(range(sample))
     t = time.perf_counter()
@@ -209,10 +332,40 @@ def cpu_baseline(w, cores, budget_lps):
     r1 = oracle.solve(w.lp, w.specs.subset(range(one)), tol=TOL, max_iter=100000, threads=1, lockstep=0,
                       want_xy=False)
     dt1 = time.perf_counter() - t
-    return {"value": int(np.sum(r.status <= 2)) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": int(np.sum(r.status <= 2)) / dt, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
+            "kind": "oracle",
             "sample": f"{sample} of {q} LPs of {w.name}, each alone, OpenMP over LPs, {dt:.1f} s",
             "single_thread_b1": {"value": int(np.sum(r1.status <= 2)) / dt1, "unit": UNIT, "cores": 1,
                                  "sample": f"{one} LPs one after another on one core, {dt1:.1f} s"}}
+
+
+def oracle_error(w, name, batch, res):
+    """Error of this run's results against the FP64 oracle, on the LPs the
+    oracle has stored results for: status agreement, the largest relative
+    objective error against the oracle's reference objective, and the largest
+    relative KKT residual of the returned (x, y) in the oracle's evaluation."""
+    import oracle
+
+    q = len(w.specs)
+    gold = golden_lps_and_ref(WORKLOADS[name]["golden"], q) if name in WORKLOADS else None
+    if gold is None:
+        return {"unavailable": "no stored oracle results for this workload and oracle source"}
+    lps, status, ref_obj, _ = gold
+    st = res["status"][lps]
+    both = (status == 0) & (st == 0)
+    err = np.abs(res["obj"][lps][both] - ref_obj[both]) / (1.0 + np.abs(ref_obj[both]))
+    kkt = []
+    for i, lp_i in enumerate(lps[:16]):
+        if st[i] != 0:
+            continue
+        r, x, y = batch.result(int(lp_i))
+        k = oracle.kkt_spec(w.lp, w.specs, int(lp_i), x, y)
+        kkt.append(max(k["rel_primal"], k["rel_dual"], k["rel_gap"]))
+    return {"lps": len(lps), "status_equal": int(np.sum(st == status)),
+            "max_rel_obj_err": float(err.max()) if err.size else None,
+            "max_oracle_rel_kkt": float(max(kkt)) if kkt else None, "kkt_lps": len(kkt),
+            "what": "against the FP64 oracle: reference objectives (rel-KKT 1e-6 or tighter) and the oracle's "
+                    "own KKT evaluation of the returned points, on the stored LPs of this batch"}
 
 
 def run_serving(args, rank, world, local):
@@ -323,7 +476,7 @@ def run_serving(args, rank, world, local):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32-iterates/f64-checks", "data": "synthetic",
+            "dtype": DTYPE_MIXED, "data": "synthetic",
             "config": {"workload": "serving: 5 power-law matrices m=1k..200k n=2m, Poisson requests of U{1..256} "
                                    "strong-branching children, warm start from the parent LP on the device",
                        "requests": len(ids), "lps": int(sum(len(sp) for _, _, sp in stream)), "tol": TOL,
@@ -387,7 +540,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sb_powerlaw", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="sb_large", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--extra-obbt", type=int, default=1,
+                    help="also time the 1024-LP bound-tightening batch once (an extra key)")
     ap.add_argument("--requests", type=int, default=160, help="serving: requests in the timed Poisson stream")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate as a fraction of capacity")
     ap.add_argument("--priorities", type=int, default=1, help="serving: stream priorities by matrix size")
@@ -433,7 +588,72 @@ def main():
     w = rank_workload(args.workload, args.seed, rank)
     if args.lps > 0 and args.lps < len(w.specs):
         w = lpgen.Workload(w.lp, w.specs.subset(range(args.lps)), w.precision, f"{w.name} (first {args.lps} LPs)")
-    max_iter = WORKLOADS[args.workload]["max_iter"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(local)
+    m = measure(args, lpb, torch, w, args.workload, dev, stream, flush, args.steps, args.warmup, dist, clocks,
+                extras=not args.no_extras, check_oracle=rank == 0 and world == 1 and args.lps == 0)
+
+    # the 1024-LP bound-tightening batch (m = n = 100k, nnz = 1M), once more
+    # as an extra key: one timed solve, its own roofline and oracle error
+    extra = None
+    if args.extra_obbt and args.workload != "obbt_square" and not args.no_extras:
+        wo = rank_workload("obbt_square", args.seed, rank)
+        mo = measure(args, lpb, torch, wo, "obbt_square", dev, stream, flush, 1, 0, dist, None, extras=False,
+                     check_oracle=rank == 0 and world == 1)
+        extra = {"workload": wo.name, "m": wo.lp.m, "n": wo.lp.n, "nnz": wo.lp.nnz, "lps_per_step": len(wo.specs),
+                 "value": mo["value"], "unit": UNIT, "ms_per_step": mo["ms_per_step"], "steps": 1,
+                 "lps_solved_per_step": mo["lps_solved_per_step"], "roofline": mo["roofline"],
+                 "time_split_ms_per_step": mo["time_split_ms_per_step"], "oracle_error": mo["oracle_error"],
+                 "polish": mo["polish"], "gpu_launches": mo["gpu_launches"]}
+        if rank == 0 and not args.no_cpu_baseline and world == 1:
+            extra["cpu_baseline"] = cpu_baseline(wo, "obbt_square", os.cpu_count() or 1, 0)
+
+    out = None
+    if rank == 0:
+        cores = os.cpu_count() or 1
+        cpu_lps = args.cpu_lps if args.cpu_lps >= 0 else WORKLOADS[args.workload]["cpu_lps"]
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, args.workload, cores, cpu_lps)
+        lp = w.lp
+        out = {
+            "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": m["dtype"], "data": "synthetic",
+            "config": {"workload": w.name, "m": lp.m, "n": lp.n, "nnz": lp.nnz, "lps_per_step": len(w.specs),
+                       "tol": TOL, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (1 GB iterate blocks) and L2 flushed between steps (256 MB "
+                             "write)" if lp.n * len(w.specs) * 4 > 256e6 else "flushed between steps (256 MB write)",
+                       "lps_solved_per_step": m["lps_solved_per_step"]},
+            "roofline": m["roofline"],
+            "time_split_ms_per_step": m["time_split_ms_per_step"],
+            "oracle_error": m["oracle_error"],
+            "cusparse_dual_spmm": m.get("cusparse"),
+            "width_sweep": m.get("width_sweep"),
+            "b1_loop": m.get("b1_loop"),
+            "latency_ms": m["latency_ms"],
+            "cpu_baseline": cpu,
+            "e2e": m.get("e2e"),
+            "gpu_launches": m["gpu_launches"],
+            "setup_ms": m["setup_ms"],
+            "polish": m["polish"],
+            "obbt_square": extra,
+            "clocks": m["clocks"],
+        }
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def measure(args, lpb, torch, w, name, dev, stream, flush, steps, warmup, dist, clocks, extras, check_oracle):
+    """Timed batched solves of workload w (graphs + programmatic dependent
+    launch, device-resident inputs), then one profiled repeat with events
+    around every launch for the roofline, the oracle error of one batch, and
+    (extras) the cuSPARSE comparison, width sweep, B=1 loop and end-to-end
+    leg through the host API."""
+    world = dist.get_world_size() if dist else 1
+    local = dev.index
+    max_iter = WORKLOADS[name]["max_iter"]
     precision = lpb.FP64 if w.precision == "fp64" else lpb.MIXED
     # timed solves: CUDA graphs and programmatic dependent launch, no per-launch events
     opts = lpb.lpb_default_options(precision=precision, profile=0, device=local, cuda_stream=stream.cuda_stream)
@@ -441,7 +661,6 @@ def main():
     specs_np = lpb.specs_from(w.specs)
     specs_dev = torch.from_numpy(specs_np.view(np.uint8).copy()).to(dev)
     q = len(w.specs)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def one_step():
         b = h.solve_dev(specs_dev, tol=TOL, max_iter=max_iter)
@@ -450,18 +669,18 @@ def main():
         b.free()
         return res, prof
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    nsolved, profs, lat = 0, [], []
+    if clocks:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    nsolved, profs = 0, []
     torch.cuda.nvtx.range_push("timed")
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()  # L2 (129 MB) flushed between timed solves
         ev[k][0].record(stream)
         res, prof = one_step()
@@ -470,55 +689,93 @@ def main():
         profs.append(prof)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     gpu_launches = int(sum(p.kernels for p in profs))
-    # per-launch kernel times: the same solves again with CUDA events around
+    switch_iters = [int(p.fp64_switch_iter) for p in profs]
+    # per-launch kernel times: the same solve again with CUDA events around
     # every launch (plain launches; graphs and PDL need no events between kernels)
     hp = lpb.Handle(w.lp, options=lpb.lpb_default_options(precision=precision, profile=1, device=local,
                                                          cuda_stream=stream.cuda_stream))
-    prof_steps = 1 if args.no_extras else max(1, min(args.steps, 3))
-    profs = []
-    for _ in range(prof_steps):
+    prof_steps = 1 if not extras else max(1, min(steps, 3))
+    pprofs = []
+    kept = None
+    for i in range(prof_steps):
         flush.zero_()
         b = hp.solve_dev(specs_dev, tol=TOL, max_iter=max_iter)
-        profs.append(b.profile())
-        b.free()
+        pprofs.append(b.profile())
+        if i == 0 and check_oracle:
+            kept = b
+        else:
+            b.free()
+    # the oracle's evaluation of one batch's results (the same LPs, bitwise the
+    # same results as the timed solves: graphs and PDL do not change them)
+    oerr = None
+    if check_oracle:
+        oerr = oracle_error(w, name, kept, kept.results())
+        kept.free()
     hp.close()
     total_ms, nsolved_all = reduce_over_ranks(dist, total_ms, nsolved, dev)
     value = nsolved_all / (total_ms / 1e3)
 
     # roofline of the dominant kernel, from the library's CUDA events on this stream
-    ms = np.array([[p.ms[i] for i in range(4)] for p in profs]).sum(0)
-    by = np.array([[p.bytes[i] for i in range(4)] for p in profs]).sum(0)
-    la = np.array([[p.launches[i] for i in range(4)] for p in profs]).sum(0)
+    ms = np.array([[p.ms[i] for i in range(4)] for p in pprofs]).sum(0)
+    by = np.array([[p.bytes[i] for i in range(4)] for p in pprofs]).sum(0)
+    la = np.array([[p.launches[i] for i in range(4)] for p in pprofs]).sum(0)
     names = ["k_primal (A~^T Y + primal step)", "k_dual (A~ Xbar + dual step)"]
     dom = int(np.argmax(ms[:2]))
     achieved = by[dom] / (ms[dom] / 1e3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic, traffic_note = ncu_traffic(["k_primal", "k_dual"][dom], args.workload)
+    traffic, traffic_note = ncu_traffic(["k_primal", "k_dual"][dom], name)
+    other = 1 - dom
+    out = {
+        "value": value, "ms_per_step": total_ms / steps, "lps_solved_per_step": nsolved / steps,
+        "dtype": "f64" if precision == lpb.FP64 else DTYPE_MIXED,
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": traffic, "traffic_note": traffic_note, "launches": int(la[dom]),
+                     "avg_launch_us": 1e3 * ms[dom] / max(la[dom], 1),
+                     "timing": f"CUDA events around every launch over {prof_steps} profiled repeat(s) of the "
+                               "timed solve (plain launches)",
+                     "other_kernel": {"kernel": names[other], "achieved": by[other] / (ms[other] / 1e3) / 1e9
+                                      if ms[other] > 0 else None,
+                                      "frac": by[other] / (ms[other] / 1e3) / 1e9 / peak if ms[other] > 0 else None,
+                                      "avg_launch_us": 1e3 * ms[other] / max(la[other], 1)}},
+        "time_split_ms_per_step": {"primal_step": ms[0] / prof_steps, "dual_step": ms[1] / prof_steps,
+                                   "check_spmm": ms[2] / prof_steps, "check_reduce": ms[3] / prof_steps,
+                                   "what": "profiled repeats (plain launches, events around each)"},
+        "oracle_error": oerr,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "what": "one batched solve"},
+        "gpu_launches": gpu_launches,
+        "setup_ms": pprofs[0].setup_ms if pprofs else None,
+        "polish": {"arith": "dfloat" if opts.polish_arith == lpb.POLISH_DFLOAT else "fp64",
+                   "switch_iter_per_step": switch_iters},
+        "clocks": clk,
+    }
+    if not extras:
+        h.close()
+        return out
 
     # the paper's engine on the same shape, and the step time against the batch
     # width (the synthetic analogue of the paper's SpMM-vs-N figure)
-    cus, width_sweep = None, None
-    if not args.no_extras:
-        try:
-            cus = cusparse_spmm(w.lp, q, dev)
-        except Exception as ex:  # torch without CSR SpMM support on this device
-            cus = {"unavailable": str(ex)[:120]}
-        # widths whose lane and check workspace fit in half the free memory
-        # (about 44 n + 36 m bytes per FP32 column)
-        per_col = 44.0 * w.lp.n + 36.0 * w.lp.m
-        free_b = torch.cuda.mem_get_info(dev)[0]
-        widths = [k for k in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096) if k * per_col < 0.5 * free_b]
-        us_w, best_w = h.tune_batch(widths)
-        width_sweep = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
-                       "best_width": widths[best_w],
-                       "what": "one iteration (primal + dual step) on N copies of the base LP, plain launches"}
+    try:
+        out["cusparse"] = cusparse_spmm(w.lp, q, dev)
+    except Exception as ex:  # torch without CSR SpMM support on this device
+        out["cusparse"] = {"unavailable": str(ex)[:120]}
+    # widths whose lane and check workspace fit in half the free memory
+    # (about 44 n + 36 m bytes per FP32 column)
+    per_col = 44.0 * w.lp.n + 36.0 * w.lp.m
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    widths = [k for k in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096) if k * per_col < 0.5 * free_b]
+    us_w, best_w = h.tune_batch(widths)
+    out["width_sweep"] = {"us_per_iteration": {str(k): round(float(u), 2) for k, u in zip(widths, us_w)},
+                          "best_width": widths[best_w],
+                          "what": "one iteration (primal + dual step) on N copies of the base LP, plain launches"}
 
     # B=1 loop: the same kernels, one LP per solve
-    b1_n = 0 if args.no_extras else min(args.b1_lps, q)
+    b1_n = min(args.b1_lps, q)
     b1_specs = [torch.from_numpy(specs_np[i:i + 1].view(np.uint8).copy()).to(dev) for i in range(b1_n)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -530,13 +787,16 @@ def main():
     torch.cuda.synchronize()
     b1_s = time.perf_counter() - t0
     b1_value = b1_solved / b1_s if b1_n > 0 else None
+    out["b1_loop"] = {"value": b1_value, "unit": UNIT, "lps": b1_n,
+                      "batched_over_b1": value / world / b1_value if b1_value else None}
+    h.close()
 
     # end to end through the public host API: create (H2D of A, vectors),
     # solve from host records, results back to the host
     lp = w.lp
     h2d = (lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.vals.nbytes + lp.c.nbytes + lp.row_lo.nbytes +
            lp.row_hi.nbytes + lp.var_lo.nbytes + lp.var_hi.nbytes + specs_np.nbytes)
-    e2e_steps = 0 if args.no_extras else max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_solved, d2h = 0, 0
@@ -549,53 +809,10 @@ def main():
         be.free()
         he.close()
     e2e_s = time.perf_counter() - t0
-    e2e_value = e2e_solved / e2e_s * (world if dist else 1) if e2e_steps else None
-
-    out = None
-    if rank == 0:
-        cores = os.cpu_count() or 1
-        cpu_lps = args.cpu_lps if args.cpu_lps >= 0 else WORKLOADS[args.workload]["cpu_lps"]
-        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, cores, cpu_lps)
-        setup_ms = profs[0].setup_ms if profs else None
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == lpb.FP64 else "f32-iterates/f64-checks", "data": "synthetic",
-            "config": {"workload": w.name, "m": lp.m, "n": lp.n, "nnz": lp.nnz, "lps_per_step": q, "tol": TOL,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed between steps (256 MB write)",
-                       "lps_solved_per_step": nsolved / args.steps},
-            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": traffic, "traffic_note": traffic_note, "launches": int(la[dom]),
-                         "avg_launch_us": 1e3 * ms[dom] / max(la[dom], 1),
-                         "timing": f"CUDA events around every launch over {prof_steps} profiled repeats of the "
-                                   "timed solve (plain launches)",
-                         "other_kernel_GBps": by[1 - dom] / (ms[1 - dom] / 1e3) / 1e9 if ms[1 - dom] > 0 else None},
-            "time_split_ms_per_step": {"primal_step": ms[0] / prof_steps, "dual_step": ms[1] / prof_steps,
-                                       "check_spmm": ms[2] / prof_steps, "check_reduce": ms[3] / prof_steps,
-                                       "what": "profiled repeats (plain launches, events around each)"},
-            "cusparse_dual_spmm": cus,
-            "width_sweep": width_sweep,
-            "b1_loop": {"value": b1_value, "unit": UNIT, "lps": b1_n,
-                        "batched_over_b1": value / world / b1_value if b1_value else None},
-            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                           "what": "one batched solve"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "what": "lpb_create from host CSR + lpb_solve from host records + lpb_results"},
-            "gpu_launches": gpu_launches,
-            "setup_ms": setup_ms,
-            "polish": {"arith": "dfloat" if opts.polish_arith == lpb.POLISH_DFLOAT else "fp64",
-                       "switch_iter_per_step": [int(p.fp64_switch_iter) for p in profs]},
-            "clocks": clk,
-        }
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    if out is not None:
-        print(json.dumps(out), flush=True)
+    out["e2e"] = {"value": e2e_solved / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(d2h), "over_value": e2e_solved / e2e_s * world / value,
+                  "what": "lpb_create from host CSR + lpb_solve from host records + lpb_results"}
+    return out
 
 
 if __name__ == "__main__":

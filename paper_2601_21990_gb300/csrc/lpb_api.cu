@@ -244,6 +244,9 @@ lpb_err apply_shape(lpb_ctx* h, Csr& c, int thr, int shift) {
     if (c.long_thr != thr) {
         c.long_thr = thr;
         CU(build_long_rows(c, h->stream));
+        // the segment scratch follows the new long-row lists
+        lpb_err rc = ensure_long_scratch(h, std::max(h->lr_cap, h->ws_cap), true);
+        if (rc != LPB_OK) return rc;
     }
     c.g_shift = shift;
     h->ws_epoch += 1;  // captured intervals hold the old launch shapes
@@ -752,8 +755,9 @@ void lpb_destroy(lpb_handle h) {
     free_list(h->ws_allocs);
     if (h->specs_dev) cudaFree(h->specs_dev);
     free_list(h->fixed_allocs);
-    if (h->A.long_rows) cudaFree(h->A.long_rows);
-    if (h->At.long_rows) cudaFree(h->At.long_rows);
+    free_long_rows(h->A);
+    free_long_rows(h->At);
+    free_long_scratch(h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

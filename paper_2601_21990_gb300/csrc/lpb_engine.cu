@@ -214,7 +214,53 @@ lpb_err lane_reserve(lpb_ctx* h, Lane& ln, int prec, int cap, int gcap) {
     return LPB_OK;
 }
 
+void free_long_scratch(lpb_ctx* h) {
+    if (h->lr_part) cudaFree(h->lr_part);
+    if (h->lr_ticket) cudaFree(h->lr_ticket);
+    h->lr_part = nullptr;
+    h->lr_ticket = nullptr;
+    for (Csr* c : {&h->A, &h->At}) {
+        c->part = nullptr;
+        c->ticket = nullptr;
+        c->ntix = 0;
+    }
+}
+
+lpb_err ensure_long_scratch(lpb_ctx* h, int cap, bool force) {
+    // partial sums: [segment][cap] of the widest iterate type (8 bytes);
+    // tickets: one per (long row, column tile), at most cap / 2 + 1 tiles
+    if (!force && cap <= h->lr_cap) return LPB_OK;
+    LPB_CU(cudaStreamSynchronize(h->stream));
+    free_long_scratch(h);
+    h->lr_cap = 0;
+    if (cap <= 0) return LPB_OK;
+    const int ntix = cap / 2 + 1;
+    const size_t segs = (size_t)h->A.n_lblocks + h->At.n_lblocks;
+    const size_t rows = (size_t)h->A.n_long + h->At.n_long;
+    if (segs > 0) {
+        LPB_CU(cudaMalloc(&h->lr_part, segs * (size_t)cap * 8));
+        LPB_CU(cudaMalloc((void**)&h->lr_ticket, rows * ntix * sizeof(unsigned)));
+        LPB_CU(cudaMemsetAsync(h->lr_ticket, 0, rows * ntix * sizeof(unsigned), h->stream));
+    }
+    char* part = (char*)h->lr_part;
+    unsigned* tick = h->lr_ticket;
+    for (Csr* c : {&h->A, &h->At}) {
+        c->ntix = ntix;
+        c->part = c->n_lblocks > 0 ? part : nullptr;
+        c->ticket = c->n_long > 0 ? tick : nullptr;
+        part += (size_t)c->n_lblocks * cap * 8;
+        tick += (size_t)c->n_long * ntix;
+    }
+    h->lr_cap = cap;
+    h->ws_epoch += 1;  // captured intervals hold the old scratch pointers
+    return LPB_OK;
+}
+
 lpb_err ensure_check_ws(lpb_ctx* h, int cap) {
+    if (cap > h->lr_cap) {
+        lpb_err rc = ensure_long_scratch(h, std::max(cap, h->ws_cap), false);
+        if (rc != LPB_OK) return rc;
+    }
     if (cap <= h->ws_cap) return LPB_OK;
     for (void* p : h->ws_allocs) cudaFree(p);
     h->ws_allocs.clear();

@@ -42,11 +42,13 @@ struct GraphKey {
     const void* rec_h = nullptr;
     const int* long_a = nullptr;        // long-row lists of A~ and A~^T
     const int* long_at = nullptr;
+    const void* part = nullptr;         // long-row segment scratch
     int n_long_a = -1, n_long_at = -1, thr_a = -1, thr_at = -1, shift_a = -1, shift_at = -1;
     bool operator==(const GraphKey& o) const {
         return ncol == o.ncol && uni == o.uni && L == o.L && stall == o.stall && ws_epoch == o.ws_epoch &&
                tsize == o.tsize && ld == o.ld && X == o.X && Y == o.Y && rec == o.rec && rec_h == o.rec_h &&
-               long_a == o.long_a && long_at == o.long_at && n_long_a == o.n_long_a && n_long_at == o.n_long_at &&
+               long_a == o.long_a && long_at == o.long_at && part == o.part && n_long_a == o.n_long_a &&
+               n_long_at == o.n_long_at &&
                thr_a == o.thr_a && thr_at == o.thr_at && shift_a == o.shift_a && shift_at == o.shift_at;
     }
 };
@@ -131,6 +133,10 @@ struct lpb_ctx {
     int ws_cap = 0;
     int ws_epoch = 0;
     double *P = nullptr, *Q = nullptr, *partials = nullptr, *colsum = nullptr;
+    // long-row segment scratch of the step kernels (A~ and A~^T share it)
+    int lr_cap = 0;
+    void* lr_part = nullptr;
+    unsigned* lr_ticket = nullptr;
     lpb_lp_spec* specs_dev = nullptr;
     int specs_cap = 0;
     std::vector<void*> ws_allocs;
@@ -158,6 +164,10 @@ lpb_err lane_reserve(lpb_ctx* h, Lane& ln, int prec, int cap, int gcap);
 void lane_free(Lane& ln);
 // check workspace for a lane of cap columns, and room for count spec records
 lpb_err ensure_check_ws(lpb_ctx* h, int cap);
+// the step kernels' long-row segment scratch for lanes of up to cap columns
+// (force: reallocate after the long-row lists changed)
+lpb_err ensure_long_scratch(lpb_ctx* h, int cap, bool force);
+void free_long_scratch(lpb_ctx* h);
 lpb_err ensure_specs(lpb_ctx* h, int count);
 // first free run of count residual slots, or -1
 int lane_find_slots(const Lane& ln, int count);
@@ -215,6 +225,7 @@ inline GraphKey interval_key(const lpb_ctx* h, const Lane& ln, int L, int stall_
     k.rec_h = ln.rec_h;
     k.long_a = h->A.long_rows;
     k.long_at = h->At.long_rows;
+    k.part = h->lr_part;
     k.n_long_a = h->A.n_long;
     k.n_long_at = h->At.n_long;
     k.thr_a = h->A.long_thr;

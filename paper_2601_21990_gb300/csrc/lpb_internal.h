@@ -68,7 +68,26 @@ struct Csr {
     int n_long = 0;
     int long_thr = kLongRow;    // rows longer than this get a whole block (tunable)
     int g_shift = 0;            // step kernels use (lanes per row from the batch width) >> g_shift
+    // Step kernels cut a long row into segments of at most kLongSeg entries,
+    // one block each, listed segment-major (every row's segment 0, then every
+    // row's segment 1, ...) so that the blocks running together gather from
+    // the same range of columns.  lseg[2 b], lseg[2 b + 1]: the long row
+    // (index into long_rows) and segment of block b; the segments of long row
+    // i are lseg0[i] .. lseg0[i + 1] - 1 in the partial-sum scratch.
+    int* lseg = nullptr;
+    int* lseg0 = nullptr;
+    int n_lblocks = 0;
+    // partial sums of multi-segment rows, [segment][ld] in the iterate type,
+    // and one completion ticket per (long row, column tile), tile stride ntix
+    void* part = nullptr;
+    unsigned* ticket = nullptr;
+    int ntix = 0;
 };
+
+#ifndef LPB_LONG_SEG
+#define LPB_LONG_SEG 1024
+#endif
+constexpr int kLongSeg = LPB_LONG_SEG;  // entries per segment of a long row in the step kernels
 
 // Per-column parameters of the iteration kernels (structure of arrays,
 // length >= ld, in the iterate precision T).
@@ -137,8 +156,10 @@ void set_last_error(const char* msg);
 // ---------------------------------------------------------------------------
 cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm_out, cudaStream_t s);
 cudaError_t exclusive_scan_i32(const int* in, int* out, int count, int* total_dev, cudaStream_t s);
-// (re)builds a.long_rows for threshold a.long_thr (frees an old list)
+// (re)builds a.long_rows and the step kernels' segments for threshold
+// a.long_thr (frees an old list); free_long_rows releases them
 cudaError_t build_long_rows(Csr& a, cudaStream_t s);
+void free_long_rows(Csr& a);
 cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& at, const double* at_vals,
                                 int ruiz_iters, int pock_chambolle, double* d_r, double* d_c,
                                 double* tmp_r, double* tmp_c, cudaStream_t s);

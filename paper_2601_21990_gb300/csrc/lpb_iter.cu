@@ -196,6 +196,12 @@ struct StepArgs {
     const T* va;
     const int* long_rows;
     int n_long, long_thr;
+    const int* lseg;  // long-row blocks: (long row, segment) of each, segment-major
+    const int* lseg0; // first segment of each long row; segments of row i: lseg0[i + 1] - lseg0[i]
+    int n_lblocks;
+    T* part;          // partial sums of multi-segment rows, [segment][ld]
+    unsigned* ticket; // completion count per (long row, column tile), tile stride ntix
+    int ntix;
     const T* src;     // gathered block: Y^k (primal) or Xbar (dual)
     // row-side state
     T* Z;             // X^k -> X^{k+1} (primal) / Y^k -> Y^{k+1} (dual), in place
@@ -322,10 +328,40 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
     }
 }
 
+__device__ __forceinline__ void stv_cg(float* p, const float (&r)[4]) {
+    __stcg(reinterpret_cast<float4*>(p), make_float4(r[0], r[1], r[2], r[3]));
+}
+__device__ __forceinline__ void stv_cg(double* p, const double (&r)[2]) {
+    __stcg(reinterpret_cast<double2*>(p), make_double2(r[0], r[1]));
+}
+__device__ __forceinline__ void stv_cg(dfloat* p, const dfloat (&r)[2]) {
+    __stcg(reinterpret_cast<float4*>(p), make_float4(r[0].hi, r[0].lo, r[1].hi, r[1].lo));
+}
+__device__ __forceinline__ void ldv_cg(const float* p, float (&r)[4]) {
+    const float4 u = __ldcg(reinterpret_cast<const float4*>(p));
+    r[0] = u.x; r[1] = u.y; r[2] = u.z; r[3] = u.w;
+}
+__device__ __forceinline__ void ldv_cg(const double* p, double (&r)[2]) {
+    const double2 u = __ldcg(reinterpret_cast<const double2*>(p));
+    r[0] = u.x; r[1] = u.y;
+}
+__device__ __forceinline__ void ldv_cg(const dfloat* p, dfloat (&r)[2]) {
+    const float4 u = __ldcg(reinterpret_cast<const float4*>(p));
+    r[0] = dfloat(u.x, u.y); r[1] = dfloat(u.z, u.w);
+}
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ dfloat add(dfloat a, dfloat b) { return a + b; }
+
 // One step (primal or dual) of the iteration on one column tile.
-//   Blocks [0, n_long): one long row each, split into contiguous pieces over
-//   the block's row groups and reduced in shared memory.
-//   Blocks [n_long, gridDim.x): persistent over the short rows, row group g
+//   Blocks [0, n_lblocks): one segment of a long row each (at most kLongSeg
+//   entries), split into contiguous pieces over the block's row groups and
+//   reduced in shared memory.  A row of one segment is finished by its block;
+//   for a row of several, each block stores its partial sums, and the block
+//   that completes the row (the last to take the row's ticket; no block
+//   waits) adds the partials in segment order and finishes the row, so the
+//   result does not depend on which block ends last.
+//   Blocks [n_lblocks, gridDim.x): persistent over the short rows, row group g
 //   taking rows g, g + stride, ...; while it gathers and finishes a row, the
 //   row pointers and the first index round of its next row are in flight.
 template <typename T, int G, bool CHECK, bool PRIMAL>
@@ -373,23 +409,52 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::v) k_step(const StepArgs
     const int colg = active ? col0 : tile0;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
 
-    if ((int)blockIdx.x < a.n_long) {
-        const int row = a.long_rows[blockIdx.x];
-        const int rb = a.rp[row], re = a.rp[row + 1];
+    if ((int)blockIdx.x < a.n_lblocks) {
+        const int li = a.lseg[2 * blockIdx.x], sg = a.lseg[2 * blockIdx.x + 1];
+        const int s0 = a.lseg0[li], ns = a.lseg0[li + 1] - s0;
+        const int row = a.long_rows[li];
+        const int rb0 = a.rp[row], re0 = a.rp[row + 1];
+        const int sl = (re0 - rb0 + ns - 1) / ns;  // entries per segment
+        const int rb = min(re0, rb0 + sg * sl), re = min(re0, rb + sl);
         const int piece = (re - rb + GPB - 1) / GPB;
         const int beg = min(re, rb + grp * piece), end = min(re, beg + piece);
         T acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = T(0);
         gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg, end, gmask, acc);
-        if (!long_row_reduce<T, V, G>(acc, red) || !active) return;
+        if (!long_row_reduce<T, V, G>(acc, red)) return;
+        // only row group 0 (lanes 0 .. G-1 of warp 0) continues
+        if (ns > 1) {
+            if (active) stv_cg(a.part + (size_t)(s0 + sg) * a.ld + col0, acc);
+            __threadfence();
+            __syncwarp(gmask);
+            unsigned last = 0;
+            if (lane == 0) {
+                unsigned* t = a.ticket + (size_t)li * a.ntix + blockIdx.y;
+                last = atomicAdd(t, 1u) == (unsigned)(ns - 1);
+                if (last) *t = 0u;  // ready for the next launch
+            }
+            last = __shfl_sync(gmask, last, 0, G);
+            if (!last) return;
+            __threadfence();
+            if (!active) return;
+            T p[V];
+            ldv_cg(a.part + (size_t)s0 * a.ld + col0, acc);
+#pragma unroll 1
+            for (int t = 1; t < ns; ++t) {
+                ldv_cg(a.part + (size_t)(s0 + t) * a.ld + col0, p);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = add(acc[v], p[v]);
+            }
+        }
+        if (!active) return;
         if (PRIMAL) primal_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc, uca, ucb);
         else dual_epilogue<T, V, TN, CHECK>(a, P, row, col0, lane * V, acc, uca, ucb);
         return;
     }
 
-    const int stride = ((int)gridDim.x - a.n_long) * GPB;
-    int r = ((int)blockIdx.x - a.n_long) * GPB + grp;
+    const int stride = ((int)gridDim.x - a.n_lblocks) * GPB;
+    int r = ((int)blockIdx.x - a.n_lblocks) * GPB + grp;
     int beg = 0, end = 0;
     int c[K];
     T av[K];
@@ -458,7 +523,7 @@ cudaError_t launch_k(const StepArgs<T>& a, cudaStream_t s) {
     const int sms = packed / 64, per_sm = packed % 64;
     const int need = (a.rows + GPB - 1) / GPB;
     const int persist = need < sms * per_sm ? need : sms * per_sm;
-    dim3 grid(a.n_long + persist, (a.ncol + TN - 1) / TN);
+    dim3 grid(a.n_lblocks + persist, (a.ncol + TN - 1) / TN);
     if (!a.pdl) {
         k_step<T, G, CHECK, PRIMAL><<<grid, kBlock, 0, s>>>(a);
         return cudaGetLastError();
@@ -512,6 +577,12 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.long_rows = d.At.long_rows;
     p.n_long = d.At.n_long;
     p.long_thr = d.At.long_thr;
+    p.lseg = d.At.lseg;
+    p.lseg0 = d.At.lseg0;
+    p.n_lblocks = d.At.n_lblocks;
+    p.part = (T*)d.At.part;
+    p.ticket = d.At.ticket;
+    p.ntix = d.At.ntix;
     p.src = b.Y;
     p.Z = b.X;
     p.Z0 = b.X0;
@@ -543,6 +614,12 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.long_rows = d.A.long_rows;
     q.n_long = d.A.n_long;
     q.long_thr = d.A.long_thr;
+    q.lseg = d.A.lseg;
+    q.lseg0 = d.A.lseg0;
+    q.n_lblocks = d.A.n_lblocks;
+    q.part = (T*)d.A.part;
+    q.ticket = d.A.ticket;
+    q.ntix = d.A.ntix;
     q.src = b.Xbar;
     q.Z = b.Y;
     q.Z0 = b.Y0;

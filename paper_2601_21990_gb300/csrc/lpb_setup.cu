@@ -5,6 +5,7 @@
 //   lists of long rows for the SpMM kernels.
 // Every kernel is deterministic: sums run in a fixed order, the transpose is
 // sorted by the original entry index inside each row of A^T.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <vector>
@@ -501,14 +502,62 @@ cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm
     return cudaFreeAsync(cnt, s);
 }
 
+// Segments of the long rows for the step kernels: long row i (length len_i)
+// gets ceil(len_i / kLongSeg) segments; blocks are listed segment-major.
+static cudaError_t build_long_segments(Csr& a, cudaStream_t s) {
+    cudaError_t e;
+    if (a.n_long == 0) return cudaSuccess;
+    std::vector<int> rows(a.n_long), beg(a.n_long), end(a.n_long);
+    if ((e = cudaMemcpyAsync(rows.data(), a.long_rows, sizeof(int) * a.n_long, cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    for (int i = 0; i < a.n_long; ++i) {
+        int pr[2];
+        if ((e = cudaMemcpy(pr, a.rp + rows[i], sizeof(int) * 2, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+        beg[i] = pr[0];
+        end[i] = pr[1];
+    }
+    std::vector<int> seg0(a.n_long + 1, 0);
+    int max_ns = 0;
+    for (int i = 0; i < a.n_long; ++i) {
+        const int ns = std::max(1, (end[i] - beg[i] + kLongSeg - 1) / kLongSeg);
+        seg0[i + 1] = seg0[i] + ns;
+        max_ns = std::max(max_ns, ns);
+    }
+    std::vector<int> lseg;
+    lseg.reserve(2 * (size_t)seg0[a.n_long]);
+    for (int sg = 0; sg < max_ns; ++sg)
+        for (int i = 0; i < a.n_long; ++i)
+            if (sg < seg0[i + 1] - seg0[i]) {
+                lseg.push_back(i);
+                lseg.push_back(sg);
+            }
+    a.n_lblocks = seg0[a.n_long];
+    if ((e = cudaMalloc((void**)&a.lseg, sizeof(int) * lseg.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&a.lseg0, sizeof(int) * seg0.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(a.lseg, lseg.data(), sizeof(int) * lseg.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    return cudaMemcpy(a.lseg0, seg0.data(), sizeof(int) * seg0.size(), cudaMemcpyHostToDevice);
+}
+
+void free_long_rows(Csr& a) {
+    if (a.long_rows) cudaFree(a.long_rows);
+    if (a.lseg) cudaFree(a.lseg);
+    if (a.lseg0) cudaFree(a.lseg0);
+    a.long_rows = nullptr;
+    a.lseg = a.lseg0 = nullptr;
+    a.n_long = a.n_lblocks = 0;
+}
+
 cudaError_t build_long_rows(Csr& a, cudaStream_t s) {
     cudaError_t e;
-    if (a.long_rows) {
+    if (a.long_rows || a.lseg) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        cudaFree(a.long_rows);
-        a.long_rows = nullptr;
+        free_long_rows(a);
     }
     a.n_long = 0;
+    a.n_lblocks = 0;
     if (a.rows == 0) return cudaSuccess;
     int *flag = nullptr, *total = nullptr;
     if ((e = cudaMallocAsync((void**)&flag, sizeof(int) * ((size_t)a.rows * 2 + 1), s)) != cudaSuccess) return e;
@@ -526,7 +575,8 @@ cudaError_t build_long_rows(Csr& a, cudaStream_t s) {
         k_long_scatter<<<grid_for(a.rows, 256), 256, 0, s>>>(flag, pos, a.rows, a.long_rows);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return cudaFreeAsync(flag, s);
+    if ((e = cudaFreeAsync(flag, s)) != cudaSuccess) return e;
+    return build_long_segments(a, s);
 }
 
 cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& at, const double* at_vals,
