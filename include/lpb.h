@@ -58,8 +58,11 @@ typedef enum {
 typedef enum { LPB_FP64 = 0, LPB_MIXED = 1 } lpb_precision;
 
 typedef struct {
-    int32_t precision;              /* LPB_FP64: FP64 iterates; LPB_MIXED: FP32 iterates and SpMM,
-                                       FP64 residuals, restart tests and scaling factors */
+    int32_t precision;              /* LPB_FP64: FP64 iterates and checks; LPB_MIXED: FP32 iterates and
+                                       SpMM, with the KKT residuals, gap, certificates and the fixed-point
+                                       residual summed in double-float arithmetic (a pair of FP32 values,
+                                       about 48 significand bits, FP32 exponent range); the restart tests,
+                                       primal weights and scaling factors are FP64 */
     int32_t check_every;            /* iterations between residual evaluations (default 64) */
     int32_t ruiz_iters;             /* Ruiz infinity-norm passes (default 10) */
     int32_t pock_chambolle;         /* 1: one Pock-Chambolle (alpha = 1) pass after Ruiz */

@@ -54,8 +54,17 @@ template <> struct Vec<float> { static constexpr int V = 4; };
 template <> struct Vec<double> { static constexpr int V = 2; };
 template <> struct Vec<dfloat> { static constexpr int V = 2; };
 
-template <typename T> struct MinBlocks { static constexpr int v = LPB_STEP_MIN_BLOCKS; };
-template <> struct MinBlocks<dfloat> { static constexpr int v = LPB_STEP_MIN_BLOCKS_DF; };
+// the FP32 primal step streams several iterate blocks besides its gathers:
+// on wide batches (row groups of 32 lanes, where 48 registers hold it
+// without spilling) it gains from more resident warps, i.e. loads in flight
+#ifndef LPB_STEP_MIN_BLOCKS_PRIMAL
+#define LPB_STEP_MIN_BLOCKS_PRIMAL 10
+#endif
+template <typename T, int G, bool PRIMAL> struct MinBlocks { static constexpr int v = LPB_STEP_MIN_BLOCKS; };
+template <int G> struct MinBlocks<float, G, true> {
+    static constexpr int v = G >= 32 ? LPB_STEP_MIN_BLOCKS_PRIMAL : LPB_STEP_MIN_BLOCKS;
+};
+template <int G, bool PRIMAL> struct MinBlocks<dfloat, G, PRIMAL> { static constexpr int v = LPB_STEP_MIN_BLOCKS_DF; };
 
 __device__ __forceinline__ void ldv(const float* p, float (&r)[4]) {
     float4 u = *reinterpret_cast<const float4*>(p);
@@ -365,7 +374,7 @@ __device__ __forceinline__ dfloat add(dfloat a, dfloat b) { return a + b; }
 //   taking rows g, g + stride, ...; while it gathers and finishes a row, the
 //   row pointers and the first index round of its next row are in flight.
 template <typename T, int G, bool CHECK, bool PRIMAL>
-__global__ void __launch_bounds__(kBlock, MinBlocks<T>::v) k_step(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(const StepArgs<T> a) {
     constexpr int V = Vec<T>::V, GPB = kBlock / G, TN = G * V;
     constexpr int K = Round<T, G>::K, R = Round<T, G>::R;
     __shared__ T red[kBlock * V];

@@ -346,8 +346,8 @@ __global__ void k_power_init(double* v, int n, uint64_t seed) {
 // leaves its share of the squared norm of the result as one partial; the
 // last block to finish (an atomic ticket, no waiting) adds the partials in
 // block order and writes the norm to a scalar the next launch reads.  The
-// grid is fixed at kPowBlocks, so the rows each block covers and the order of
-// every sum are the same on every run.  The normalisation v = w / ||w|| is
+// grid is fixed at kPowBlocks plus one block per long row, so the rows each
+// block covers and the order of every sum are the same on every run.  The normalisation v = w / ||w|| is
 // applied after the forward product, u = (A~ w) / ||w||, so no launch writes
 // v and none only reduces.
 #ifndef LPB_POW_BLOCKS
@@ -386,29 +386,47 @@ __device__ __forceinline__ void finish_norm(double* part, unsigned* __restrict__
     }
 }
 
-// y = M x (divided by *nrm_x when nrm_x is given), kPowGroup lanes per row;
-// *nrm_y = ||y|| (and hist[slot] = ||y|| when hist is given).
+// y = M x (divided by *nrm_x when nrm_x is given); *nrm_y = ||y|| (and
+// hist[slot] = ||y|| when hist is given).  Blocks [0, n_long) take one of the
+// rows longer than long_thr each, all threads striding over its entries;
+// the other blocks take the remaining rows with kPowGroup lanes per row.
 __global__ void __launch_bounds__(kPowThreads) k_power_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                                             const double* __restrict__ v, int rows,
-                                                            const double* __restrict__ x,
+                                                            const int* __restrict__ long_rows, int n_long,
+                                                            int long_thr, const double* __restrict__ x,
                                                             const double* __restrict__ nrm_x,
                                                             double* __restrict__ y, double* part,
                                                             unsigned* __restrict__ ticket, double* __restrict__ nrm_y,
                                                             double* __restrict__ hist, int slot) {
     __shared__ double sh[32];
     const double nx = nrm_x ? *nrm_x : 1.0;
+    if ((int)blockIdx.x < n_long) {
+        const int i = long_rows[blockIdx.x];
+        double acc = 0.0;
+        for (int e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) acc += v[e] * x[ci[e]];
+        const double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) {
+            const double yi = !nrm_x ? t : (nx > 0.0 ? t / nx : 0.0);
+            y[i] = yi;
+            part[blockIdx.x] = yi * yi;
+        }
+        finish_norm(part, ticket, nrm_y, hist, slot, sh);
+        return;
+    }
     constexpr int kRowsPerWarp = 32 / kPowGroup;
     const int lane = threadIdx.x % kPowGroup, sub = (threadIdx.x & 31) / kPowGroup;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = (((int)blockIdx.x - n_long) * blockDim.x + threadIdx.x) >> 5;
+    const int warps = (((int)gridDim.x - n_long) * blockDim.x) >> 5;
     double sq = 0.0;  // the group's rows in order, in its first lane
     // the loop bound is the same for the whole warp, so every lane reaches the shuffles
     for (int base = warp * kRowsPerWarp; base < rows; base += warps * kRowsPerWarp) {
         const int i = base + sub;
         double acc = 0.0;
-        if (i < rows)
+        const bool mine = i < rows && rp[i + 1] - rp[i] <= long_thr;
+        if (mine)
             for (int e = rp[i] + lane; e < rp[i + 1]; e += kPowGroup) acc += v[e] * x[ci[e]];
         for (int o = kPowGroup / 2; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, kPowGroup);
-        if (lane == 0 && i < rows) {
+        if (lane == 0 && mine) {
             const double yi = !nrm_x ? acc : (nx > 0.0 ? acc / nx : 0.0);
             y[i] = yi;
             sq += yi * yi;
@@ -677,8 +695,9 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
     return cudaFreeAsync(part, s);
 }
 
-size_t power_work_doubles(int m, int n, int max_iter) {
-    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + 3 + 2 * ((size_t)max_iter + 1);
+size_t power_work_doubles(int m, int n, int max_iter, int n_long_max) {
+    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + (size_t)n_long_max + 3 +
+           2 * ((size_t)max_iter + 1);
 }
 
 // Power iteration on A~^T A~: sigma_est = ||A~ v|| for unit v.  Stops at the
@@ -689,12 +708,13 @@ size_t power_work_doubles(int m, int n, int max_iter) {
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
                        double* est_out, int* iters_out, cudaStream_t s) {
     const int m = a.rows, n = a.cols;
-    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks), ||u||, ||w||, the
-    // ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the unnormalised start vector
+    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks + the larger long-row
+    // count), ||u||, ||w||, the ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the
+    // unnormalised start vector
     double* w = work;
     double* u = w + n;
     double* part = u + (m > 0 ? m : 1);
-    double* nrm_u = part + kPowBlocks;
+    double* nrm_u = part + kPowBlocks + (a.n_long > at.n_long ? a.n_long : at.n_long);
     double* nrm_w = nrm_u + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(nrm_w + 1);
     double* hist_est = nrm_w + 2;
@@ -707,17 +727,21 @@ cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, ui
     k_power_init<<<grid_for(n, 256), 256, 0, s>>>(w, n, seed);
     k_power_norm<<<kPowBlocks, kPowThreads, 0, s>>>(w, n, part, ticket, nrm_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    constexpr int kChunk = 64;
+    // products queued between two looks at the history (products past the
+    // stopping point are wasted work)
+    constexpr int kChunk = 16;
     std::vector<double> he(kChunk), hn(kChunk);
     double prev = -1.0;
     for (int base = 1; base <= max_iter; base += kChunk) {
         const int last = base + kChunk - 1 < max_iter ? base + kChunk - 1 : max_iter;
         for (int it = base; it <= last; ++it) {
             // u = A~ w / ||w|| (records ||u||), then w = A~^T u (records ||w||)
-            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, w, nrm_w, u, part, ticket, nrm_u,
-                                                            hist_est, it);
-            k_power_spmv<<<kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, u, nullptr, w, part, ticket,
-                                                            nrm_w, hist_nw, it);
+            k_power_spmv<<<a.n_long + kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, a.long_rows, a.n_long,
+                                                                         a.long_thr, w, nrm_w, u, part, ticket, nrm_u,
+                                                                         hist_est, it);
+            k_power_spmv<<<at.n_long + kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, at.long_rows,
+                                                                          at.n_long, at.long_thr, u, nullptr, w, part,
+                                                                          ticket, nrm_w, hist_nw, it);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int cnt = last - base + 1;
