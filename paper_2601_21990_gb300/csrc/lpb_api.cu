@@ -513,7 +513,7 @@ lpb_err lpb_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, co
         double hs[2] = {0.0, 0.0};
         CU(cudaMemcpyAsync(hs, scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
         double* work = nullptr;
-        const size_t wn = power_work_doubles(m, n, o.power_max_iter, std::max(h->A.n_long, h->At.n_long));
+        const size_t wn = power_work_doubles(m, n, nnz, o.power_max_iter);
         CU(dmalloc(tmp.v, &work, sizeof(double) * wn));
         double est = 0.0;
         int its = 0;

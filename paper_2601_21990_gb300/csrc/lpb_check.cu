@@ -307,12 +307,17 @@ __global__ void k_colsum(const double* __restrict__ part, int nb_m, int nb_n, in
 // iterations k0 .. k0+ce-1 of group g's next interval, computed once in FP64
 // so that the iteration kernels do no division; thread `me` of `nth` writes
 // every nth entry.
+// Group g's Halpern weights (k+1)/(k+2), 1/(k+2) of Eq. mainiter for the
+// interval that starts at inner index k0: entry e = 0 .. ce holds index
+// k0 - 1 + e, so iteration t uses entry t + 1 and the primal step rebuilds
+// its iterate with entry t; at k0 = 0 (a start or a restart) entry 0 is
+// (0, 1): the iterate is the anchor.
 __device__ __forceinline__ void write_halpern(double* hal64, float* hal32, dfloat* haldf, int g, int k0, int ce,
                                               int me, int nth) {
-    for (int t = me; t < ce; t += nth) {
-        const double k = (double)k0 + t;
+    for (int t = me; t <= ce; t += nth) {
+        const double k = (double)k0 - 1.0 + t;
         const double ca = (k + 1.0) / (k + 2.0), cb = 1.0 / (k + 2.0);
-        const size_t h = 2 * ((size_t)g * ce + t);
+        const size_t h = 2 * ((size_t)g * (ce + 1) + t);
         hal64[h] = ca;
         hal64[h + 1] = cb;
         hal32[h] = (float)ca;
@@ -482,23 +487,41 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(const DecideArgs<T> a
 }
 
 // On a restart of a column's group: anchor and iterate <- T(z) at the check
-// (or the anchor <- the Halpern iterate for restart_to_output = 0).
+// (or the anchor <- the Halpern iterate for restart_to_output = 0).  The
+// dual side keeps its iterate Z; the primal side keeps only the reflected
+// point Zbar, from which the next step rebuilds the iterate (with weights
+// 0 and 1 after a restart), and sets it to the new anchor as well.
 template <typename T>
-__global__ void k_restart_copy(T* __restrict__ Z, T* __restrict__ Z0, const T* __restrict__ Zh, int rows, int ld,
-                               int ncol, int to_output, const int* __restrict__ grp, const Control* __restrict__ ctl,
+__global__ void k_restart_copy(T* __restrict__ Z, T* __restrict__ Zbar, T* __restrict__ Z0,
+                               const T* __restrict__ Zh, int rows, int ld, int ncol, int to_output,
+                               const int* __restrict__ grp, const Control* __restrict__ ctl,
                                const int* __restrict__ flags) {
     if (!flags[0]) return;
     const size_t total = (size_t)rows * ld;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(p % ld);
         if (j >= ncol || !ctl[grp[j]].restart) continue;
-        if (to_output) {
-            const T v = Zh[p];
-            Z[p] = v;
-            Z0[p] = v;
-        } else {
-            Z0[p] = Z[p];
-        }
+        const T v = to_output ? Zh[p] : Z[p];
+        if (Z && to_output) Z[p] = v;
+        if (Zbar) Zbar[p] = v;
+        Z0[p] = v;
+    }
+}
+
+// The primal Halpern iterate after an interval of L iterations,
+// X = (k+1)/(k+2) Xbar + X^0/(k+2) with the weights of the interval's last
+// iteration (entry L of the column's group), for the checks of
+// restart_to_output = 0, which read the iterate itself.
+template <typename T>
+__global__ void k_halpern_iterate(T* __restrict__ X, const T* __restrict__ Xbar, const T* __restrict__ X0,
+                                  const T* __restrict__ hal, const int* __restrict__ grp, int rows, int ld, int ncol,
+                                  int ce, int L) {
+    const size_t total = (size_t)rows * ld;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(p % ld);
+        if (j >= ncol) continue;
+        const size_t h = 2 * ((size_t)grp[j] * (ce + 1) + L);
+        X[p] = hal[h] * Xbar[p] + hal[h + 1] * X0[p];
     }
 }
 
@@ -626,8 +649,10 @@ __global__ void k_init_columns(const InitArgs<T> a) {
 // admitted columns; LP q's warm start is warm_x + q * wsx (n values) and
 // warm_y + q * wsy (m values): column-major blocks, or one vector for every
 // LP with stride 0
+// (the primal side stores the reflected point Xbar, from which the first
+// step rebuilds the iterate with weights 0 and 1: it starts equal to X0)
 template <typename T>
-__global__ void k_init_iterates(const InitArgs<T> a, T* X, T* X0, T* Y, T* Y0, const double* warm_x,
+__global__ void k_init_iterates(const InitArgs<T> a, T* Xbar, T* X0, T* Y, T* Y0, const double* warm_x,
                                 const double* warm_y, long long wsx, long long wsy) {
     const size_t nx = (size_t)a.n * a.count, ny = (size_t)a.m * a.count;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < nx + ny; p += (size_t)gridDim.x * blockDim.x) {
@@ -641,7 +666,7 @@ __global__ void k_init_iterates(const InitArgs<T> a, T* X, T* X0, T* Y, T* Y0, c
             T t = w < hi ? w : hi;
             const T v = t > lo ? t : lo;
             const size_t e = (size_t)i * a.ld + j;
-            X[e] = v;
+            Xbar[e] = v;
             X0[e] = v;
         } else {
             const size_t r = p - nx;
@@ -677,7 +702,8 @@ __global__ void k_extract(int n, int m, int ld, const int* __restrict__ cols, do
     }
 }
 
-// moves column src[p] -> dst[p] in every row of the state blocks
+// moves column src[p] -> dst[p] in every row of the state blocks (the
+// primal reflected point Xbar and anchor X0, the dual iterate and anchor)
 template <typename T>
 __global__ void k_compact_rows(T* X, T* X0, T* Y, T* Y0, int n, int m, int ld, const int* __restrict__ src,
                                const int* __restrict__ dst, int count) {
@@ -1049,6 +1075,14 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     double* Q2 = Q + 2 * (size_t)n * ld;
     constexpr bool kDf = !std::is_same<T, double>::value;  // FP32 or dfloat iterates
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    if (!d.restart_to_output) {
+        // the checks of the literal restart reading read the Halpern iterate
+        const T* hal = std::is_same<T, double>::value ? (const T*)d.hal64
+                       : std::is_same<T, float>::value ? (const T*)d.hal32 : (const T*)d.haldf;
+        k_halpern_iterate<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.Xbar, b.X0, hal, d.col.grp, n, ld,
+                                                                             ncol, d.check_every, interval_len);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // A~ [x^, x^ - x] and A~^T [y^, Pi_B(y^ - y), y^ - y]: in double-float for
     // FP32 iterates, in FP64 for FP64 iterates (P and Q hold either)
     if constexpr (kDf) {
@@ -1182,10 +1216,10 @@ cudaError_t launch_check(const CheckData& d, const IterBufs<T>& b, int ld, int n
     da.flags = d.flags;
     k_decide<T><<<1, kDecideThreads, 0, s>>>(da);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_restart_copy<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.X0, b.Xh, n, ld, ncol,
+    k_restart_copy<T><<<blocks_for((size_t)n * ld, 256), 256, 0, s>>>(b.X, b.Xbar, b.X0, b.Xh, n, ld, ncol,
                                                                       d.restart_to_output, d.col.grp, d.ctl, d.flags);
     if (m > 0)
-        k_restart_copy<T><<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(b.Y, b.Y0, b.Yh, m, ld, ncol,
+        k_restart_copy<T><<<blocks_for((size_t)m * ld, 256), 256, 0, s>>>(b.Y, nullptr, b.Y0, b.Yh, m, ld, ncol,
                                                                           d.restart_to_output, d.col.grp, d.ctl,
                                                                           d.flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1227,7 +1261,7 @@ cudaError_t launch_admit(const CheckData& d, const IterData<T>& it, const IterBu
     k_init_columns<T><<<(count + 255) / 256, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_init_iterates<T><<<blocks_for((size_t)(d.n + d.m) * count, 256), 256, 0, s>>>(a, b.X, b.X0, b.Y, b.Y0, warm_x,
+    k_init_iterates<T><<<blocks_for((size_t)(d.n + d.m) * count, 256), 256, 0, s>>>(a, b.Xbar, b.X0, b.Y, b.Y0, warm_x,
                                                                                     warm_y, wsx, wsy);
     return cudaGetLastError();
 }
@@ -1248,7 +1282,7 @@ template <typename T>
 cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int* src_dev, const int* dst_dev,
                            int count, ColParams<T> colp, ColCheck colc, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    k_compact_rows<T><<<blocks_for((size_t)(n + m) * count, 256), 256, 0, s>>>(b.X, b.X0, b.Y, b.Y0, n, m, ld,
+    k_compact_rows<T><<<blocks_for((size_t)(n + m) * count, 256), 256, 0, s>>>(b.Xbar, b.X0, b.Y, b.Y0, n, m, ld,
                                                                                 src_dev, dst_dev, count);
     k_compact_cols<T><<<(count + 255) / 256, 256, 0, s>>>(colp, colc, src_dev, dst_dev, count);
     return cudaGetLastError();
@@ -1256,7 +1290,8 @@ cudaError_t launch_compact(const IterBufs<T>& b, int n, int m, int ld, const int
 
 namespace {
 
-// state of column sc of the FP32 lane -> column dc of the polish lane
+// state of column sc of the FP32 lane (the reflected point Xbar, the anchors,
+// the dual iterate) -> column dc of the polish lane
 template <typename TD>
 __global__ void k_migrate_rows(const float* __restrict__ X, const float* __restrict__ X0,
                                const float* __restrict__ Y, const float* __restrict__ Y0, TD* __restrict__ DXs,
@@ -1323,7 +1358,7 @@ cudaError_t launch_migrate(const CheckData& src, const IterBufs<float>& sb, int 
     if (count <= 0) return cudaSuccess;
     const int n = src.n, m = src.m;
     k_migrate_rows<TD><<<blocks_for((size_t)(n + m) * count, 256), 256, 0, s>>>(
-        sb.X, sb.X0, sb.Y, sb.Y0, db.X, db.X0, db.Y, db.Y0, n, m, lds, ldd, sc_dev, dc_dev, count);
+        sb.Xbar, sb.X0, sb.Y, sb.Y0, db.Xbar, db.X0, db.Y, db.Y0, n, m, lds, ldd, sc_dev, dc_dev, count);
     k_migrate_cols<TD><<<(count + 255) / 256, 256, 0, s>>>(src.col, dst.col, dcolp, sc_dev, dc_dev, count, group_dst,
                                                            slot_shift, src.d_c, src.eta);
     return cudaGetLastError();

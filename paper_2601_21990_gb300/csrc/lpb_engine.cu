@@ -177,8 +177,11 @@ lpb_err lane_reserve(lpb_ctx* h, Lane& ln, int prec, int cap, int gcap) {
     const size_t n = (size_t)h->n, mr = h->m > 0 ? (size_t)h->m : 1;
     const int ce = h->opt.check_every;
     const int nslot = 2 * cap;
-    void** xs[] = {&ln.X, &ln.X0, &ln.Xbar, &ln.Xh, &ln.DX};
+    // the primal iterate itself is not stored (the steps rebuild it from Xbar
+    // and X0); the checks of the literal restart reading need it
+    void** xs[] = {&ln.X0, &ln.Xbar, &ln.Xh, &ln.DX};
     for (void** q : xs) LPB_CU(dmalloc(L, (char**)q, n * cap * tsz));
+    if (!h->opt.restart_to_pdhg_output) LPB_CU(dmalloc(L, (char**)&ln.X, n * cap * tsz));
     void** ys[] = {&ln.Y, &ln.Y0, &ln.Yh, &ln.DY, &ln.DYp};
     for (void** q : ys) LPB_CU(dmalloc(L, (char**)q, mr * cap * tsz));
     void** cs[] = {&ln.clo, &ln.chi, &ln.cc, &ln.ctau, &ln.csigma};
@@ -192,9 +195,9 @@ lpb_err lane_reserve(lpb_ctx* h, Lane& ln, int prec, int cap, int gcap) {
     LPB_CU(cudaMemset(ln.ctl, 0, sizeof(Control) * gcap));
     LPB_CU(dmalloc(L, &ln.flags, sizeof(int) * 4));
     LPB_CU(cudaMemset(ln.flags, 0, sizeof(int) * 4));
-    LPB_CU(dmalloc(L, &ln.hal64, sizeof(double) * 2 * (size_t)gcap * ce));
-    LPB_CU(dmalloc(L, &ln.hal32, sizeof(float) * 2 * (size_t)gcap * ce));
-    LPB_CU(dmalloc(L, &ln.haldf, sizeof(dfloat) * 2 * (size_t)gcap * ce));
+    LPB_CU(dmalloc(L, &ln.hal64, sizeof(double) * 2 * (size_t)gcap * (ce + 1)));
+    LPB_CU(dmalloc(L, &ln.hal32, sizeof(float) * 2 * (size_t)gcap * (ce + 1)));
+    LPB_CU(dmalloc(L, &ln.haldf, sizeof(dfloat) * 2 * (size_t)gcap * (ce + 1)));
     LPB_CU(dmalloc(L, &ln.rscr, sizeof(double) * nslot));
     LPB_CU(dmalloc(L, &ln.rtag, sizeof(int) * nslot));
     LPB_CU(cudaMemset(ln.rtag, 0, sizeof(int) * nslot));
@@ -361,10 +364,10 @@ double step_bytes(int prec, int nnz, int m, int n, bool primal, bool check, int 
     const double ts = prec == kPrecF32 ? 4.0 : 8.0;
     const double rows = primal ? n : m, cols = primal ? m : n;
     double b = (4.0 + ts) * nnz + 4.0 * (rows + 1);
-    // gathered block once, plus the row-side operands: primal reads X, X0 and
-    // writes X, Xbar; dual reads Y, Y0 and writes Y; a check writes x^, dx
+    // gathered block once, plus the row-side operands: primal reads Xbar, X0
+    // and writes Xbar; dual reads Y, Y0 and writes Y; a check writes x^, dx
     // (primal) or y^, dy, Pi_B(dy) (dual)
-    b += ts * ncol * (cols + rows * (primal ? 4.0 : 3.0) + (check ? (primal ? 2.0 : 3.0) * rows : 0.0));
+    b += ts * ncol * (cols + rows * 3.0 + (check ? (primal ? 2.0 : 3.0) * rows : 0.0));
     return b;
 }
 

@@ -36,7 +36,7 @@ enum LanePrec { kPrecF32 = 0, kPrecF64 = 1, kPrecDfl = 2 };
 struct GraphKey {
     int ncol = -1, uni = -1, L = -1, stall = -1, ws_epoch = -1, tsize = 0;
     int ld = -1;
-    const void* X = nullptr;            // lane iterate blocks (all allocated together)
+    const void* X = nullptr;            // lane iterate blocks (all allocated together): Xbar
     const void* Y = nullptr;
     const void* rec = nullptr;          // per-column records and their pinned mirror
     const void* rec_h = nullptr;
@@ -219,7 +219,7 @@ inline GraphKey interval_key(const lpb_ctx* h, const Lane& ln, int L, int stall_
     k.ws_epoch = h->ws_epoch;
     k.tsize = tsize;
     k.ld = ln.cap;
-    k.X = ln.X;
+    k.X = ln.Xbar;
     k.Y = ln.Y;
     k.rec = ln.rec;
     k.rec_h = ln.rec_h;

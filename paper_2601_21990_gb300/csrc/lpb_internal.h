@@ -165,8 +165,8 @@ cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& a
                                 double* tmp_r, double* tmp_c, cudaStream_t s);
 cudaError_t scale_values(const Csr& a, const double* a_vals, const double* d_r, const double* d_c,
                          bool rows_are_constraints, double* out64, float* out32, cudaStream_t s);
-// doubles of device work space power_norm needs for an m x n matrix
-size_t power_work_doubles(int m, int n, int max_iter, int n_long_max);
+// doubles of device work space power_norm needs for an m x n matrix of nnz entries
+size_t power_work_doubles(int m, int n, long long nnz, int max_iter);
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed,
                        double* work, double* est_out, int* iters_out, cudaStream_t s);
 cudaError_t scale_vectors(int m, int n, const double* d_r, const double* d_c, const double* c,

@@ -2,9 +2,13 @@
 // whole active batch (Sec. 5, Eq. batched_iter and main-iterate).
 //
 //   primal step  (rows of A~^T, one per variable i; G = A~^T Y^k):
+//     X^k_ij = k/(k+1) Xb_ij + X^0_ij/(k+1)   (the previous Halpern update,
+//                                              rebuilt from the stored Xb)
 //     x^  = Pi_[xlo_ij, xhi_ij](X^k_ij - tau_j (c_ij + G_ij))
 //     xb  = 2 x^ - X^k_ij                     (the reflection, also A(2x - x^k))
-//     X^{k+1}_ij = (k+1)/(k+2) xb + X^0_ij/(k+2)
+//     X^{k+1}_ij = (k+1)/(k+2) xb + X^0_ij/(k+2), not stored: the next
+//     primal step rebuilds it from xb, which the dual step needs anyway
+//     (at k = 0 the weights are 0 and 1, so X^0 itself)
 //   dual step    (rows of A~, one per constraint i; H = A~ Xb):
 //     v   = Y^k_ij / sigma_j + H_ij
 //     y^  = sigma_j (v - Pi_[l_i,u_i](v))     (= Y + sigma H - sigma Pi(Y/sigma + H))
@@ -213,9 +217,9 @@ struct StepArgs {
     int ntix;
     const T* src;     // gathered block: Y^k (primal) or Xbar (dual)
     // row-side state
-    T* Z;             // X^k -> X^{k+1} (primal) / Y^k -> Y^{k+1} (dual), in place
+    T* Z;             // dual: Y^k -> Y^{k+1}, in place (unused by the primal step)
     const T* Z0;      // anchor
-    T* Zbar;          // primal: Xbar out
+    T* Zbar;          // primal: Xbar of the previous iteration in, the new Xbar out (in place)
     T* Zh;            // check: x^ / y^
     T* DZ;            // check: x^ - X^k / y^ - Y^k
     T* Aux;           // check, dual: Pi_B(y^ - Y^k)
@@ -224,7 +228,9 @@ struct StepArgs {
     const T* rhi;
     ColParams<T> col;
     int ld, ncol;
-    const T* hal;     // per group g: (k+1)/(k+2), 1/(k+2) of Eq. mainiter at [2 (g ce + t)]
+    const T* hal;     // per group g, entry e = 0 .. ce: (k+1)/(k+2), 1/(k+2) of Eq. mainiter
+                      // for k = k_start - 1 + e at [2 (g (ce + 1) + e)]; iteration t of the
+                      // interval uses entry t + 1, and entry t rebuilds its X^k
     int t, ce;
     int uni;          // the group of every active column, or -1 if they belong to several
     int pdl;          // launched as a programmatic dependent of the previous step kernel
@@ -259,24 +265,28 @@ __device__ __forceinline__ T barrier(T v, T lo, T hi) {
 // ca, cb are the Halpern weights of the column's restart group
 template <typename T, int TN>
 struct TileParams {
-    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN], ca[TN], cb[TN];
+    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN], ca[TN], cb[TN], pa[TN], pb[TN];
     int kind[TN], var[TN];
 };
 
 // primal epilogue for row `row`, lane columns col0 .. col0+V (q0 = their
-// offset in the tile): box projection, reflection, Halpern update
+// offset in the tile): the iterate rebuilt from the previous reflection,
+// box projection, reflection (the Halpern update of Eq. mainiter is applied
+// when the next step rebuilds its iterate)
 template <typename T, int V, int TN, bool CHECK>
 __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const TileParams<T, TN>& P, int row, int col0,
-                                                int q0, const T (&acc)[V], T uca, T ucb) {
+                                                int q0, const T (&acc)[V], T upa, T upb) {
     const size_t off = (size_t)row * a.ld + col0;
     T x[V], x0[V];
-    ldv(a.Z + off, x);
+    ldv(a.Zbar + off, x);
     ldv(a.Z0 + off, x0);
     const T cr = a.rc[row], lor = a.rlo[row], hir = a.rhi[row];
-    T xh[V], xb[V], xn[V], dz[V];
+    T xh[V], xb[V], dz[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int q = q0 + v;
+        const T pa = a.uni >= 0 ? upa : P.pa[q], pb = a.uni >= 0 ? upb : P.pb[q];
+        x[v] = mad(pa, x[v], pb * x0[v]);  // X^k = k/(k+1) Xb + X^0/(k+1)
         const int kind = P.kind[q], var = P.var[q];
         T cj = cr, lo = lor, hi = hir;
         if (kind == 2) cj = var == row ? P.c[q] : T(0);
@@ -288,15 +298,12 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
         s = s > lo ? s : lo;
         xh[v] = s;
         xb[v] = T(2) * s - x[v];
-        const T ca = a.uni >= 0 ? uca : P.ca[q], cb = a.uni >= 0 ? ucb : P.cb[q];
-        xn[v] = ca * xb[v] + cb * x0[v];
         // x^ - x: where the box is not active it is -tau (c + G) exactly,
         // which stays accurate when |x| is large (diverging iterates of an
         // infeasible LP); elsewhere the difference with the bound
         dz[v] = inside ? -step : s - x[v];
     }
     stv(a.Zbar + off, xb);
-    stv(a.Z + off, xn);
     if (CHECK) {
         stv(a.Zh + off, xh);
         stv(a.DZ + off, dz);
@@ -385,9 +392,16 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
         const int j = tile0 + q;
         const bool in = j < a.ncol;
         if (a.uni < 0) {
-            const int h = in ? 2 * (a.col.grp[j] * a.ce + a.t) : 0;
-            P.ca[q] = in ? a.hal[h] : T(0);
-            P.cb[q] = in ? a.hal[h + 1] : T(0);
+            // entry t + 1 of the column's group: this iteration's weights;
+            // entry t: the previous iteration's, which rebuild X^k
+            const int h = in ? 2 * (a.col.grp[j] * (a.ce + 1) + a.t + 1) : 2;
+            if (PRIMAL) {
+                P.pa[q] = in ? a.hal[h - 2] : T(0);
+                P.pb[q] = in ? a.hal[h - 1] : T(0);
+            } else {
+                P.ca[q] = in ? a.hal[h] : T(0);
+                P.cb[q] = in ? a.hal[h + 1] : T(0);
+            }
         }
         if (PRIMAL) {
             P.kind[q] = in ? a.col.kind[j] : 0;
@@ -411,7 +425,8 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
     // one restart group in the whole batch: its Halpern weights as scalars
-    const int hu = a.uni >= 0 ? 2 * (a.uni * a.ce + a.t) : 0;
+    // (the primal step takes the previous iteration's, the dual step this one's)
+    const int hu = a.uni >= 0 ? 2 * (a.uni * (a.ce + 1) + a.t + (PRIMAL ? 0 : 1)) : 0;
     const T uca = a.uni >= 0 ? a.hal[hu] : T(0), ucb = a.uni >= 0 ? a.hal[hu + 1] : T(0);
     const int col0 = tile0 + lane * V;
     const bool active = col0 < a.ncol;
@@ -593,7 +608,7 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.ticket = d.At.ticket;
     p.ntix = d.At.ntix;
     p.src = b.Y;
-    p.Z = b.X;
+    p.Z = nullptr;
     p.Z0 = b.X0;
     p.Zbar = b.Xbar;
     p.Zh = b.Xh;

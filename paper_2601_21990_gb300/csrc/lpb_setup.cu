@@ -196,6 +196,12 @@ __global__ void k_long_flags(const int* __restrict__ rp, int rows, int thr, int*
         flag[i] = (rp[i + 1] - rp[i]) > thr ? 1 : 0;
 }
 
+__global__ void k_long_lengths(const int* __restrict__ rp, const int* __restrict__ rows, int count,
+                               int* __restrict__ len) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        len[i] = rp[rows[i] + 1] - rp[rows[i]];
+}
+
 __global__ void k_long_scatter(const int* __restrict__ flag, const int* __restrict__ pos, int rows,
                                int* __restrict__ list) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
@@ -388,8 +394,9 @@ __device__ __forceinline__ void finish_norm(double* part, unsigned* __restrict__
 
 // y = M x (divided by *nrm_x when nrm_x is given); *nrm_y = ||y|| (and
 // hist[slot] = ||y|| when hist is given).  Blocks [0, n_long) take one of the
-// rows longer than long_thr each, all threads striding over its entries;
-// the other blocks take the remaining rows with kPowGroup lanes per row.
+// rows longer than long_thr (a list of them) each, all threads striding over
+// its entries; the other blocks take the remaining rows with kPowGroup lanes
+// per row.
 __global__ void __launch_bounds__(kPowThreads) k_power_spmv(const int* __restrict__ rp, const int* __restrict__ ci,
                                                             const double* __restrict__ v, int rows,
                                                             const int* __restrict__ long_rows, int n_long,
@@ -525,21 +532,20 @@ cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm
 static cudaError_t build_long_segments(Csr& a, cudaStream_t s) {
     cudaError_t e;
     if (a.n_long == 0) return cudaSuccess;
-    std::vector<int> rows(a.n_long), beg(a.n_long), end(a.n_long);
-    if ((e = cudaMemcpyAsync(rows.data(), a.long_rows, sizeof(int) * a.n_long, cudaMemcpyDeviceToHost, s)) !=
+    std::vector<int> len(a.n_long);
+    int* len_dev = nullptr;
+    if ((e = cudaMallocAsync((void**)&len_dev, sizeof(int) * a.n_long, s)) != cudaSuccess) return e;
+    k_long_lengths<<<grid_for(a.n_long, 256), 256, 0, s>>>(a.rp, a.long_rows, a.n_long, len_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(len.data(), len_dev, sizeof(int) * a.n_long, cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
         return e;
+    if ((e = cudaFreeAsync(len_dev, s)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    for (int i = 0; i < a.n_long; ++i) {
-        int pr[2];
-        if ((e = cudaMemcpy(pr, a.rp + rows[i], sizeof(int) * 2, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
-        beg[i] = pr[0];
-        end[i] = pr[1];
-    }
     std::vector<int> seg0(a.n_long + 1, 0);
     int max_ns = 0;
     for (int i = 0; i < a.n_long; ++i) {
-        const int ns = std::max(1, (end[i] - beg[i] + kLongSeg - 1) / kLongSeg);
+        const int ns = std::max(1, (len[i] + kLongSeg - 1) / kLongSeg);
         seg0[i + 1] = seg0[i] + ns;
         max_ns = std::max(max_ns, ns);
     }
@@ -695,8 +701,10 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
     return cudaFreeAsync(part, s);
 }
 
-size_t power_work_doubles(int m, int n, int max_iter, int n_long_max) {
-    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + (size_t)n_long_max + 3 +
+// (at most nnz / kLongSeg rows have more than kLongSeg entries: one block
+// and one norm partial each)
+size_t power_work_doubles(int m, int n, long long nnz, int max_iter) {
+    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + (size_t)(nnz / kLongSeg + 1) + 3 +
            2 * ((size_t)max_iter + 1);
 }
 
@@ -705,16 +713,21 @@ size_t power_work_doubles(int m, int n, int max_iter, int n_long_max) {
 // ||A~^T A~ v|| = 0, or after max_iter products.  The host looks at the
 // history every kChunk products; products past the stopping point change
 // nothing that is returned.
+static cudaError_t power_iterate(const Csr& a, const Csr& at, const Csr& va, const Csr& vat, int max_iter,
+                                 double tol, uint64_t seed, double* part, double* nrm_u, double* nrm_w,
+                                 unsigned* ticket, double* hist_est, double* hist_nw, double* w, double* u,
+                                 double* est_out, int* iters_out, cudaStream_t s);
+
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
                        double* est_out, int* iters_out, cudaStream_t s) {
     const int m = a.rows, n = a.cols;
-    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks + the larger long-row
-    // count), ||u||, ||w||, the ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the
+    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks + nnz / kLongSeg + 1),
+    // ||u||, ||w||, the ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the
     // unnormalised start vector
     double* w = work;
     double* u = w + n;
     double* part = u + (m > 0 ? m : 1);
-    double* nrm_u = part + kPowBlocks + (a.n_long > at.n_long ? a.n_long : at.n_long);
+    double* nrm_u = part + kPowBlocks + (size_t)a.nnz / kLongSeg + 1;
     double* nrm_w = nrm_u + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(nrm_w + 1);
     double* hist_est = nrm_w + 2;
@@ -723,6 +736,33 @@ cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, ui
     *est_out = 0.0;
     *iters_out = 0;
     if (m == 0 || a.nnz == 0) return cudaSuccess;
+    // the rows of more than kLongSeg entries of A~ and A~^T, one block each
+    Csr va = a, vat = at;
+    for (Csr* c : {&va, &vat}) {
+        c->long_rows = c->lseg = c->lseg0 = nullptr;
+        c->long_thr = kLongSeg;
+        if ((e = build_long_rows(*c, s)) != cudaSuccess) {
+            free_long_rows(va);
+            free_long_rows(vat);
+            return e;
+        }
+    }
+    e = power_iterate(a, at, va, vat, max_iter, tol, seed, part, nrm_u, nrm_w, ticket, hist_est, hist_nw, w, u,
+                      est_out, iters_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free_long_rows(va);
+    free_long_rows(vat);
+    return e;
+}
+
+// The products of power_norm; va and vat list the rows of more than kLongSeg
+// entries of A~ and A~^T.
+static cudaError_t power_iterate(const Csr& a, const Csr& at, const Csr& va, const Csr& vat, int max_iter,
+                                 double tol, uint64_t seed, double* part, double* nrm_u, double* nrm_w,
+                                 unsigned* ticket, double* hist_est, double* hist_nw, double* w, double* u,
+                                 double* est_out, int* iters_out, cudaStream_t s) {
+    const int m = a.rows, n = a.cols;
+    cudaError_t e;
     if ((e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     k_power_init<<<grid_for(n, 256), 256, 0, s>>>(w, n, seed);
     k_power_norm<<<kPowBlocks, kPowThreads, 0, s>>>(w, n, part, ticket, nrm_w);
@@ -736,12 +776,13 @@ cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, ui
         const int last = base + kChunk - 1 < max_iter ? base + kChunk - 1 : max_iter;
         for (int it = base; it <= last; ++it) {
             // u = A~ w / ||w|| (records ||u||), then w = A~^T u (records ||w||)
-            k_power_spmv<<<a.n_long + kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, a.long_rows, a.n_long,
-                                                                         a.long_thr, w, nrm_w, u, part, ticket, nrm_u,
-                                                                         hist_est, it);
-            k_power_spmv<<<at.n_long + kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, at.long_rows,
-                                                                          at.n_long, at.long_thr, u, nullptr, w, part,
-                                                                          ticket, nrm_w, hist_nw, it);
+            // rows of more than kLongSeg entries get a whole block each
+            k_power_spmv<<<va.n_long + kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, va.long_rows,
+                                                                          va.n_long, kLongSeg, w, nrm_w, u, part,
+                                                                          ticket, nrm_u, hist_est, it);
+            k_power_spmv<<<vat.n_long + kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, vat.long_rows,
+                                                                           vat.n_long, kLongSeg, u, nullptr, w, part,
+                                                                           ticket, nrm_w, hist_nw, it);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int cnt = last - base + 1;

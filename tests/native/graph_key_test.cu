@@ -16,7 +16,7 @@ static void expect_change(const char* what, F mutate) {
     auto setup = [](lpb_ctx& hh, lpb::Lane& l) {
         l.cap = 128;
         l.ncol = 100;
-        l.X = reinterpret_cast<void*>(0x1000);
+        l.Xbar = reinterpret_cast<void*>(0x1000);
         l.Y = reinterpret_cast<void*>(0x2000);
         l.rec = reinterpret_cast<lpb::ColRecord*>(0x3000);
         l.rec_h = reinterpret_cast<lpb::ColRecord*>(0x4000);
@@ -48,7 +48,7 @@ static void expect_change(const char* what, F mutate) {
 int main() {
     expect_change("the active column count", [](lpb_ctx&, lpb::Lane& l) { l.ncol = 99; });
     expect_change("the leading dimension", [](lpb_ctx&, lpb::Lane& l) { l.cap = 256; });
-    expect_change("the iterate buffers", [](lpb_ctx&, lpb::Lane& l) { l.X = reinterpret_cast<void*>(0x7000); });
+    expect_change("the primal buffers", [](lpb_ctx&, lpb::Lane& l) { l.Xbar = reinterpret_cast<void*>(0x7000); });
     expect_change("the dual buffers", [](lpb_ctx&, lpb::Lane& l) { l.Y = reinterpret_cast<void*>(0x7000); });
     expect_change("the record buffer", [](lpb_ctx&, lpb::Lane& l) {
         l.rec = reinterpret_cast<lpb::ColRecord*>(0x7000);
@@ -64,6 +64,7 @@ int main() {
     expect_change("A's long-row count", [](lpb_ctx& h, lpb::Lane&) { h.A.n_long = 400; });
     expect_change("A's long-row threshold", [](lpb_ctx& h, lpb::Lane&) { h.A.long_thr = 64; });
     expect_change("A^T's lane shift", [](lpb_ctx& h, lpb::Lane&) { h.At.g_shift = 2; });
+    expect_change("the long-row scratch", [](lpb_ctx& h, lpb::Lane&) { h.lr_part = reinterpret_cast<void*>(0x7000); });
     {
         lpb_ctx h;
         lpb::Lane ln;
