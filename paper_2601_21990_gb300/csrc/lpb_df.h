@@ -173,6 +173,20 @@ LPB_HD dfloat dfl_fma(dfloat a, dfloat x, dfloat acc) {
     return dfl_of(quick_two_sum(s.hi, e));
 }
 
+// acc + a * x for a running dot product whose low part is left unnormalised
+// (the dot product in twice the working precision of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), with the
+// low parts of a and x included): the high part follows the FP32 sum through
+// TwoSum, every rounding error and the products' low parts collect in lo, and
+// dfl_norm renormalises once at the end.  Its dependent chain per term is the
+// TwoSum on the high part alone.
+LPB_HD dfloat dfl_dot_acc(dfloat a, dfloat x, dfloat acc) {
+    const df p = two_prod(a.hi, x.hi);
+    const df s = two_sum(acc.hi, p.hi);
+    return dfloat(s.hi, acc.lo + (s.lo + fmaf(a.hi, x.lo, fmaf(a.lo, x.hi, p.lo))));
+}
+LPB_HD dfloat dfl_norm(dfloat a) { return dfl_of(two_sum(a.hi, a.lo)); }
+
 // acc += w * x for a df constant and a dfloat x (the check SpMMs)
 LPB_HD void df_fma_acc(df& acc, df w, dfloat x) {
     const df p = two_prod(w.hi, x.hi);

@@ -121,7 +121,18 @@ __device__ __forceinline__ dfloat shfl(unsigned mask, dfloat v, int src, int wid
 }
 __device__ __forceinline__ float mad(float a, float x, float acc) { return fmaf(a, x, acc); }
 __device__ __forceinline__ double mad(double a, double x, double acc) { return fma(a, x, acc); }
+// the SpMM's running sums: for dfloat the low part stays unnormalised until
+// fin() (dfl_dot_acc), which shortens the dependent chain per nonzero
 __device__ __forceinline__ dfloat mad(dfloat a, dfloat x, dfloat acc) { return dfl_fma(a, x, acc); }
+__device__ __forceinline__ float dot_acc(float a, float x, float acc) { return fmaf(a, x, acc); }
+__device__ __forceinline__ double dot_acc(double a, double x, double acc) { return fma(a, x, acc); }
+__device__ __forceinline__ dfloat dot_acc(dfloat a, dfloat x, dfloat acc) { return dfl_dot_acc(a, x, acc); }
+template <int V> __device__ __forceinline__ void fin(float (&)[V]) {}
+template <int V> __device__ __forceinline__ void fin(double (&)[V]) {}
+template <int V> __device__ __forceinline__ void fin(dfloat (&acc)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = dfl_norm(acc[v]);
+}
 __device__ __forceinline__ bool is_inf(float v) { return isinf(v); }
 __device__ __forceinline__ bool is_inf(double v) { return isinf(v); }
 __device__ __forceinline__ bool is_inf(dfloat v) { return isinf(v.hi); }
@@ -182,7 +193,7 @@ __device__ __forceinline__ void gather_round(const int (&c)[Round<T, G>::K], con
 #pragma unroll
         for (int j = 0; j < B; ++j)
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = mad(aa[j], xs[j][v], acc[v]);
+            for (int v = 0; v < V; ++v) acc[v] = dot_acc(aa[j], xs[j][v], acc[v]);
     }
 }
 
@@ -446,6 +457,7 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = T(0);
         gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg, end, gmask, acc);
+        fin<V>(acc);
         if (!long_row_reduce<T, V, G>(acc, red)) return;
         // only row group 0 (lanes 0 .. G-1 of warp 0) continues
         if (ns > 1) {
@@ -503,6 +515,7 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
             gather_round<T, V, G>(c, av, min(R, end - beg), a.src, a.ld, colg, gmask, acc);
             if (end - beg > R)
                 gather_range<T, V, G>(a.ci, a.va, a.src, a.ld, colg, beg + R, end, gmask, acc);
+            fin<V>(acc);
         }
         // the next row's first index round, issued before this row's epilogue
         if (rn < a.rows) load_round<T, G>(a.ci, a.va, nbeg, nend - nbeg <= a.long_thr ? nend : nbeg, c, av);

@@ -60,6 +60,28 @@ int main() {
         acc = lpb::quick_two_sum(acc.hi, acc.lo);
         CHECK(std::fabs(val(acc) - exact) <= 1e-11 * mag, "df_fma_acc %g vs %g (mag %g)", val(acc), exact, mag);
     }
+    // dfloat dot products with the low part left unnormalised until the end
+    // (dfl_dot_acc + dfl_norm) against FP64 and against the renormalising
+    // dfl_fma: both within the twice-working-precision bound of the sum of
+    // the terms' magnitudes
+    for (int t = 0; t < 2000; ++t) {
+        const int len = 1 + (int)(rng() % 64);
+        lpb::dfloat acc(0.0f), ref(0.0f);
+        double exact = 0.0, mag = 0.0;
+        for (int e = 0; e < len; ++e) {
+            const lpb::dfloat a(u(rng) * 10.0), x(u(rng) * std::ldexp(1.0, (int)(rng() % 20) - 10));
+            acc = lpb::dfl_dot_acc(a, x, acc);
+            ref = lpb::dfl_fma(a, x, ref);
+            const double ad = (double)a.hi + (double)a.lo, xd = (double)x.hi + (double)x.lo;
+            exact += ad * xd;
+            mag += std::fabs(ad * xd);
+        }
+        acc = lpb::dfl_norm(acc);
+        const double got = (double)acc.hi + (double)acc.lo, want = (double)ref.hi + (double)ref.lo;
+        CHECK(std::fabs(got - exact) <= 1e-13 * mag, "dfl_dot_acc %g vs %g (mag %g)", got, exact, mag);
+        CHECK(std::fabs(want - exact) <= 1e-13 * mag, "dfl_fma %g vs %g (mag %g)", want, exact, mag);
+        CHECK(std::fabs(acc.lo) <= std::ldexp(std::fabs(acc.hi), -23), "dfl_norm leaves |lo| <= ulp(hi)/2");
+    }
     // infinite bounds: compared, never subtracted
     const float inf = INFINITY;
     const df pinf{inf, 0.f}, minf{-inf, 0.f}, one{1.f, 0.f}, two{2.f, 0.f};
