@@ -50,9 +50,9 @@ WORKLOADS = {
                         golden="sb_powerlaw_seed0"),
     "sb_small": dict(fn=lambda seed: lpgen.sb_small(seed=seed), max_iter=100000, cpu_lps=16, golden=None),
     "obbt_square": dict(fn=lambda seed: lpgen.obbt_square(seed=seed), max_iter=100000, cpu_lps=0,
-                        golden="obbt_square_seed0_subset16"),
+                        golden="obbt_square_seed0_subset"),
     "sb_large": dict(fn=lambda seed: lpgen.sb_large(seed=seed), max_iter=100000, cpu_lps=0,
-                     golden="sb_large_seed0_subset16"),
+                     golden="sb_large_seed0_subset"),
 }
 DTYPE_MIXED = "f32-iterates/double-float-checks"
 # iterations of the oracle's bounded sample (per LP) where whole solves take minutes

@@ -245,7 +245,7 @@ def sb_powerlaw(seed: int = 0, m: int = 20000, n: int = 50000, children: int = 6
     rng = np.random.default_rng(seed + 1000)
     cand = rng.choice(n, size=children // 2, replace=False)
     return Workload(lp, sb_specs(lp.x0, cand), "mixed",
-                    f"sb_powerlaw m={m} n={n} B={children} fp32-iterates/fp64-checks")
+                    f"sb_powerlaw m={m} n={n} B={children} fp32-iterates/double-float-checks")
 
 
 def obbt_square(seed: int = 0, m: int = 100000, n: int = 100000, lps: int = 1024,
@@ -271,7 +271,7 @@ def obbt_square(seed: int = 0, m: int = 100000, n: int = 100000, lps: int = 1024
     _rows_around(lp, x0, rng)
     cand = rng.choice(n, size=lps // 2, replace=False)
     return Workload(lp, obbt_specs(cand), "mixed",
-                    f"obbt_square m={m} n={n} B={lps} fp32-iterates/fp64-checks")
+                    f"obbt_square m={m} n={n} B={lps} fp32-iterates/double-float-checks")
 
 
 def sb_large(seed: int = 0, m: int = 1000000, n: int = 2000000, dense_rows: int = 500,
@@ -292,7 +292,7 @@ def sb_large(seed: int = 0, m: int = 1000000, n: int = 2000000, dense_rows: int 
     _rows_around(lp, x0, rng)
     cand = rng.choice(n, size=children // 2, replace=False)
     return Workload(lp, sb_specs(x0, cand), "mixed",
-                    f"sb_large m={m} n={n} B={children} fp32-iterates/fp64-checks")
+                    f"sb_large m={m} n={n} B={children} fp32-iterates/double-float-checks")
 
 
 def covering_large_bounds(seed: int = 0, m: int = 300, n: int = 500, big: float = 1e10) -> Workload:

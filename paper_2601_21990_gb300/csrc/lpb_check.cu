@@ -820,7 +820,30 @@ __global__ void __launch_bounds__(kBlock) k_spmm_df(const SpmmDfArgs<TI> a) {
     const TI* src[3] = {a.s0, a.s1, a.s2};
     if (active) {
         const int end = a.rp[row + 1];
-        for (int e = a.rp[row] + slot; e < end; e += nslot) {
+        int e = a.rp[row] + slot;
+        // four of the slot's entries per round: their gathers are issued
+        // together (loads in flight), the sums still taken in entry order
+        for (; e + 3 * nslot < end; e += 4 * nslot) {
+            int c[4];
+            df w[4];
+            TI x[4][NOPS][V];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                c[k] = a.ci[e + k * nslot];
+                w[k] = df{a.vhi[e + k * nslot], a.vlo[e + k * nslot]};
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int q = 0; q < NOPS; ++q) ldg_it(src[q] + (size_t)c[k] * a.ld + col0, x[k][q]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int q = 0; q < NOPS; ++q)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) df_fma_acc(acc[q][v], w[k], x[k][q][v]);
+        }
+        for (; e < end; e += nslot) {
             const int c = a.ci[e];
             const df w = df{a.vhi[e], a.vlo[e]};
 #pragma unroll
@@ -998,9 +1021,12 @@ __global__ void k_reduce_n_df(const ReduceDfArgs<TI> a) {
 // entries in double-float (the warp shares the row's entries, each thread
 // gathers its column) and folds them straight into the per-column
 // statistics, so the three n x N products never go to memory.
+// (four resident blocks per SM: the batched gathers would otherwise take the
+// registers of a fourth block)
 template <typename TI>
-__global__ void k_check_n_df(const ReduceDfArgs<TI> a, const int* __restrict__ rp, const int* __restrict__ ci,
-                             const float* __restrict__ vhi, const float* __restrict__ vlo) {
+__global__ void __launch_bounds__(32 * kReduceRows, 4)
+    k_check_n_df(const ReduceDfArgs<TI> a, const int* __restrict__ rp, const int* __restrict__ ci,
+                 const float* __restrict__ vhi, const float* __restrict__ vlo) {
     const int j = blockIdx.y * 32 + threadIdx.x;
     const bool ok = j < a.ncol;
     const int jj = ok ? j : blockIdx.y * 32;  // lanes past the last LP read a valid column
@@ -1009,10 +1035,35 @@ __global__ void k_check_n_df(const ReduceDfArgs<TI> a, const int* __restrict__ r
     const int kind = a.col.kind[jj], var = a.col.var[jj];
     const df olo = df_from(a.col.lo[jj]), ohi = df_from(a.col.hi[jj]), oc = df_from(a.col.c[jj]);
     for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.n; i += gridDim.x * kReduceRows) {
-        // A~^T [y^, Pi_B(dy), dy] for row i, column j
+        // A~^T [y^, Pi_B(dy), dy] for row i, column j: the gathers of four
+        // entries are issued together (loads in flight), the sums still taken
+        // in entry order
         df q0 = df_zero(), q1 = df_zero(), q2 = df_zero();
         const int end = rp[i + 1];
-        for (int e = rp[i]; e < end; ++e) {
+        int e = rp[i];
+        for (; e + 4 <= end; e += 4) {
+            size_t src[4];
+            df w[4];
+            TI g0[4], g1[4], g2[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                src[k] = (size_t)ci[e + k] * a.ld + jj;
+                w[k] = df{vhi[e + k], vlo[e + k]};
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                g0[k] = a.Yh[src[k]];
+                g1[k] = a.DYp[src[k]];
+                g2[k] = a.DY[src[k]];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                df_fma_acc(q0, w[k], g0[k]);
+                df_fma_acc(q1, w[k], g1[k]);
+                df_fma_acc(q2, w[k], g2[k]);
+            }
+        }
+        for (; e < end; ++e) {
             const size_t src = (size_t)ci[e] * a.ld + jj;
             const df w = df{vhi[e], vlo[e]};
             df_fma_acc(q0, w, a.Yh[src]);

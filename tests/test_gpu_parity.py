@@ -20,6 +20,9 @@ OBJ_TOL = 1e-4
 KKT_TOL = 1e-4
 GPU_TOL = 1e-5
 REF_TOL = 1e-7
+# the fraction of the 1024 OBBT LPs solved at tol 1e-4 within the 100k-iteration cap
+# (1019 measured on GB300)
+OBBT_SOLVED_FRACTION = 0.99
 
 
 @pytest.fixture(scope="module")
@@ -67,6 +70,52 @@ def golden_ref(name):
     assert g["oracle_sha256"] == hashlib.sha256(src).hexdigest(), "stale golden file: rerun make_reference.py"
     c = g["cases"][name]
     return _Ref(c["status"], c["obj"])
+
+
+def golden_subset(name):
+    """The oracle's stored results on a seeded subset of a full-size batch
+    (tests/golden/make_reference.py): LP indices, status and iterations at
+    rel-KKT 1e-4, status and reference objective at rel-KKT 1e-5."""
+    import hashlib
+    import json
+    import os
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    g = json.load(open(os.path.join(here, "golden", "reference_objectives.json")))
+    src = open(os.path.join(os.path.dirname(here), "oracle", "pdhg_oracle.c"), "rb").read()
+    assert g["oracle_sha256"] == hashlib.sha256(src).hexdigest(), "stale golden file: rerun make_reference.py"
+    assert name in g["cases"], f"golden case {name} missing: rerun make_reference.py {name}"
+    return g["cases"][name]
+
+
+def assert_subset_parity(orc, w, batch, res, gold, rows, lps, status_key, obj_key=None, may_hit_cap=()):
+    """Per-LP parity on the stored subset of a full-size batch.  rows[i] is
+    the batch row of the subset's LP lps[i]; the GPU's status equals the
+    oracle's (an LP listed in may_hit_cap may instead end at the iteration
+    limit), the oracle's KKT evaluation of every returned optimal point is
+    within KKT_TOL, and, with obj_key, the objectives of LPs both sides solve
+    agree with the oracle's reference objective to OBJ_TOL.  Returns the
+    number of LPs compared as optimal."""
+    checked = 0
+    for i, (row, q) in enumerate(zip(rows, lps)):
+        st_ref = gold[status_key][i]
+        st = int(res["status"][row])
+        if st == lpb_ITERATION_LIMIT and q in may_hit_cap:
+            continue
+        assert st == st_ref, (q, st, st_ref)
+        if st != 0:
+            continue
+        if obj_key is not None:
+            f_ref = gold[obj_key][i]
+            assert abs(res["obj"][row] - f_ref) / (1.0 + abs(f_ref)) <= OBJ_TOL, (q, res["obj"][row], f_ref)
+        r, x, y = batch.result(int(row))
+        k = orc.kkt_spec(w.lp, w.specs, int(q), x, y)
+        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= KKT_TOL, (q, k)
+        checked += 1
+    return checked
+
+
+lpb_ITERATION_LIMIT = 3
 
 
 def _child(lp, specs, q):
@@ -172,6 +221,20 @@ def test_sb_small(lpb, orc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_literal_restart_reading(lpb, orc, precision):
+    """Sec. 4 "Restarts" read literally (restart_to_pdhg_output = 0): the new
+    anchor is the Halpern iterate rather than T(z).  The GPU keeps only the
+    reflected point between steps and rebuilds the iterate for these checks;
+    results against the oracle run with the same reading."""
+    w = lpgen.sb_small(seed=0)
+    ref = oracle_ref(orc, w.lp, w.specs, restart_to_pdhg_output=0)
+    h = lpb.Handle(w.lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED, restart_to_pdhg_output=0)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    res = assert_parity(orc, w.lp, w.specs, b, ref)
+    assert np.sum(res["restarts"]) > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_robust_reduced_cost_large_bounds(lpb, orc, precision):
     """The stopping test with the reduced cost robust to large bounds (Sec. 4,
     after Eq. stopping) on covering LPs with 1e10 upper bounds: statuses,
@@ -225,25 +288,29 @@ def test_obbt_reduced(lpb, orc):
     assert_parity(orc, w.lp, w.specs, b, ref, kkt_lps=[0, 33])
 
 
-def test_obbt_square_full_size_properties(lpb, orc):
-    """m=n=100k, nnz=1M, B=1024: at full size the oracle checks sampled
-    outputs one by one (KKT of the returned points) and properties that hold
-    at any size: min x_j <= x0_j <= max x_j for the feasible generating point
-    x0, both within the variable's box."""
+def test_obbt_square_full_size(lpb, orc):
+    """m=n=100k, nnz=1M, B=1024 in the benchmark's configuration (tol 1e-4,
+    the 100k-iteration cap of the paper's OBBT runs, Table 2).  On the
+    oracle's stored seeded subset of 16 LPs: the status equals the oracle's
+    at the same tolerance, and the oracle's KKT evaluation of each returned
+    point is within 1e-4.  On the whole batch, properties that hold at any
+    size: the fraction of LPs solved within the cap (1019 of 1024 measured),
+    min x_j <= x0_j <= max x_j for the feasible generating point x0, both
+    within the variable's box.  Then the subset alone at tol 1e-5, so that
+    the 1e-4 objective bound has margin: statuses and objectives against the
+    oracle at rel-KKT 1e-5."""
     w = lpgen.obbt_square(seed=0)
+    gold = golden_subset("obbt_square_seed0_subset")
+    lps = gold["lps"]
+    # the oracle needs more than 50k iterations for these LPs of the subset
+    hard = [q for q, it in zip(lps, gold["iters"]) if it > 50000]
     h = lpb.Handle(w.lp, precision=lpb.MIXED)
-    # the iteration cap of the paper's OBBT runs (Table 2: 100k iterations)
     b = h.solve(w.specs, tol=1e-4, max_iter=100000)
     res = b.results()
     p = len(w.specs) // 2
     assert np.all((res["status"] == 0) | (res["status"] == 3)), np.bincount(res["status"])
-    assert np.mean(res["status"] == 0) >= 0.5, np.bincount(res["status"])
-    for q in (0, 1, 511, 512, 700, 1023):
-        if res["status"][q] != 0:
-            continue
-        r, x, y = b.result(q)
-        k = orc.kkt_spec(w.lp, w.specs, q, x, y)
-        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-4, (q, k)
+    assert np.mean(res["status"] == 0) >= OBBT_SOLVED_FRACTION, np.bincount(res["status"])
+    assert assert_subset_parity(orc, w, b, res, gold, lps, lps, "status", may_hit_cap=hard) >= 8
     lo_obj, hi_obj = res["obj"][:p], -res["obj"][p:]
     var = w.specs.var[:p]
     ok = (res["status"][:p] == 0) & (res["status"][p:] == 0)
@@ -253,6 +320,14 @@ def test_obbt_square_full_size_properties(lpb, orc):
     assert np.all(hi_obj[ok] >= x0[ok] - 1e-3 * scale[ok])
     assert np.all(lo_obj[ok] >= w.lp.var_lo[var][ok] - 1e-3 * scale[ok])
     assert np.all(hi_obj[ok] <= w.lp.var_hi[var][ok] + 1e-3 * scale[ok])
+    b.free()
+    sp = w.specs.subset(lps)
+    bs = h.solve(sp, tol=GPU_TOL, max_iter=100000)
+    rs = bs.results()
+    hard_ref = [q for q, st in zip(lps, gold["ref_status"]) if st == lpb_ITERATION_LIMIT]
+    ws = lpgen.Workload(w.lp, sp, w.precision, w.name)
+    assert assert_subset_parity(orc, ws, bs, rs, gold, list(range(len(lps))), list(range(len(lps))), "ref_status",
+                                "ref_obj", may_hit_cap=[i for i, q in enumerate(lps) if q in hard + hard_ref]) >= 8
 
 
 # ---------------------------------------------------------------------------
@@ -647,22 +722,23 @@ def test_autotune_and_batch_size_by_timing(lpb, orc):
     assert us.shape == (4,) and np.all(us > 0) and 0 <= best < 4
 
 
-def test_sb_large_full_size_properties(lpb, orc):
-    """m=1M, n=2M, nnz~10.5M (500 dense rows of 10k), B=128 as the bench runs
-    it: every LP ends optimal or certified infeasible, sampled LPs pass the
-    oracle's KKT evaluation, and no strong-branching child's optimum lies
-    below the parent LP's (Sec. 5.1: a child only shrinks the box)."""
+def test_sb_large_full_size(lpb, orc):
+    """m=1M, n=2M, nnz~10.5M (500 dense rows of 10k), B=128 in the benchmark's
+    configuration (tol 1e-4): every LP ends optimal or certified infeasible;
+    on the oracle's stored seeded subset, each status equals the oracle's at
+    the same tolerance and the oracle's KKT evaluation of each returned point
+    is within 1e-4; no strong-branching child's optimum lies below the parent
+    LP's (Sec. 5.1: a child only shrinks the box).  Then the whole batch at
+    tol 1e-5, so that the 1e-4 objective bound has margin: the subset's
+    statuses and objectives against the oracle at rel-KKT 1e-5."""
     w = lpgen.sb_large(seed=0)
+    gold = golden_subset("sb_large_seed0_subset")
+    lps = gold["lps"]
     h = lpb.Handle(w.lp, precision=lpb.MIXED)
     b = h.solve(w.specs, tol=1e-4, max_iter=100000)
     res = b.results()
     assert np.all(res["status"] <= 2), np.bincount(res["status"])
-    for q in (0, 1, 63, 64, 127):
-        if res["status"][q] != 0:
-            continue
-        r, x, y = b.result(q)
-        k = orc.kkt_spec(w.lp, w.specs, q, x, y)
-        assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= 1e-4, (q, k)
+    assert assert_subset_parity(orc, w, b, res, gold, lps, lps, "status") >= 4
     parent = h.solve(lpb.specs_array([0], [-1]), tol=1e-6, max_iter=100000).results()
     assert parent["status"][0] == 0
     f0 = parent["obj"][0]
@@ -670,3 +746,8 @@ def test_sb_large_full_size_properties(lpb, orc):
     # children at rel-gap 1e-4 may sit that far below their own optimum
     slack = 2e-4 * (1.0 + np.abs(res["obj"][opt]) + abs(f0))
     assert np.all(res["obj"][opt] >= f0 - slack), (res["obj"][opt].min(), f0)
+    b.free()
+    b5 = h.solve(w.specs, tol=GPU_TOL, max_iter=100000)
+    r5 = b5.results()
+    assert np.all(r5["status"] <= 2), np.bincount(r5["status"])
+    assert assert_subset_parity(orc, w, b5, r5, gold, lps, lps, "ref_status", "ref_obj") >= 4
