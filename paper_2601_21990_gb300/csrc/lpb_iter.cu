@@ -428,9 +428,14 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
     __syncthreads();
     // Programmatic dependent launch: everything above reads only data that
     // the previous kernel does not write (per-column parameters, Halpern
-    // weights); wait for it to complete before touching the iterates, then
-    // let the next step kernel start its own prologue on the SMs this grid
-    // frees.
+    // weights).  That holds because only step kernels after an interval's
+    // first are launched as programmatic dependents, and their predecessor
+    // is a step kernel; the first primal step of an interval follows the
+    // check, admission, extraction, compaction and migration kernels that do
+    // write those parameters, and is launched without the attribute
+    // (launch_iteration).  Wait for the predecessor to complete before
+    // touching the iterates, then let the next step kernel start its own
+    // prologue on the SMs this grid frees.
     if (a.pdl) {
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
