@@ -450,6 +450,35 @@ def test_ragged_and_multi_tile_batches(lpb, orc):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_long_rows_in_segments_over_several_tiles(lpb, orc, precision):
+    """Rows longer than one segment (1024 entries) are split over several
+    blocks whose last one finishes the row.  Four rows of 2500 entries (three
+    segments each) among rows of 3-8, 136 LPs (16 distinct children repeated:
+    two column tiles of 128 FP32 LPs with a ragged second tile, three of 64
+    FP64 LPs), with the default launch shape and with the lane shift 1 (more,
+    narrower tiles): every LP against the oracle, and the tickets of one
+    launch must be ready for the next (both shapes solve twice)."""
+    w = lpgen.sb_large(seed=1, m=3000, n=6000, dense_rows=4, dense_len=2500, children=16)
+    ref = oracle_ref(orc, w.lp, w.specs)
+    idx = np.arange(136) % 16
+    h = lpb.Handle(w.lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED)
+    first = None
+    for shift in (0, 1):
+        h.set_tuning(lpb.Tuning(32, 32, shift, shift))
+        for _ in range(2):
+            res = h.solve(w.specs.subset(idx), tol=GPU_TOL, max_iter=200000).results()
+            np.testing.assert_array_equal(res["status"], ref.status[idx])
+            err = np.abs(res["obj"] - ref.obj[idx]) / (1 + np.abs(ref.obj[idx]))
+            assert err.max() <= OBJ_TOL, (shift, err.max())
+            if first is None:
+                first = res
+            elif shift == 0:
+                # the same launch shape again: bitwise the same results
+                np.testing.assert_array_equal(res["obj"], first["obj"])
+                np.testing.assert_array_equal(res["iters"], first["iters"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_halpern_trajectory_closed_form(lpb, precision):
     """The iteration itself, not only its limit: one variable, no rows, box
     [-1, 1], cost 1e-3, so eta = 0.998, w = 1 and T(z) = z - delta with
