@@ -104,6 +104,36 @@ __device__ __forceinline__ void stv(dfloat* p, const dfloat (&r)[2]) {
     *reinterpret_cast<float4*>(p) = make_float4(r[0].hi, r[0].lo, r[1].hi, r[1].lo);
 }
 
+// The row-side operands of the epilogues (the iterate, anchor and reflected
+// blocks, and the check outputs) are each read or written once per launch.
+// When the gathered block is too large to stay in L2 anyway (StepArgs::
+// stream), they take the streaming cache hint (evict first), so that L2
+// keeps more of the gathered block, which is read once per nonzero.  When
+// everything fits in L2 the hint would evict what the next step reads.
+#ifndef LPB_STREAM_HINT
+#define LPB_STREAM_HINT 1
+#endif
+template <typename T, int V>
+__device__ __forceinline__ void lds(const T* p, T (&r)[V], bool stream) {
+    static_assert(sizeof(T) * V == sizeof(float4), "one 16-byte vector per lane");
+    if (LPB_STREAM_HINT && stream) {
+        const float4 u = __ldcs(reinterpret_cast<const float4*>(p));
+        memcpy(&r, &u, 16);
+    } else {
+        ldv(p, r);
+    }
+}
+template <typename T, int V>
+__device__ __forceinline__ void sts(T* p, const T (&r)[V], bool stream) {
+    if (LPB_STREAM_HINT && stream) {
+        float4 u;
+        memcpy(&u, &r, 16);
+        __stcs(reinterpret_cast<float4*>(p), u);
+    } else {
+        stv(p, r);
+    }
+}
+
 // scalar read-only load, shuffle, multiply-add and infinity test for each
 // iterate type
 __device__ __forceinline__ float ldg1(const float* p) { return __ldg(p); }
@@ -245,6 +275,7 @@ struct StepArgs {
     int t, ce;
     int uni;          // the group of every active column, or -1 if they belong to several
     int pdl;          // launched as a programmatic dependent of the previous step kernel
+    int stream;       // the gathered block exceeds half of L2: streaming hints on the row operands
 };
 
 // Reduce the row groups' partial sums of a long row through shared memory;
@@ -289,8 +320,8 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
                                                 int q0, const T (&acc)[V], T upa, T upb) {
     const size_t off = (size_t)row * a.ld + col0;
     T x[V], x0[V];
-    ldv(a.Zbar + off, x);
-    ldv(a.Z0 + off, x0);
+    lds(a.Zbar + off, x, a.stream);
+    lds(a.Z0 + off, x0, a.stream);
     const T cr = a.rc[row], lor = a.rlo[row], hir = a.rhi[row];
     T xh[V], xb[V], dz[V];
 #pragma unroll
@@ -314,10 +345,10 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
         // infeasible LP); elsewhere the difference with the bound
         dz[v] = inside ? -step : s - x[v];
     }
-    stv(a.Zbar + off, xb);
+    sts(a.Zbar + off, xb, a.stream);
     if (CHECK) {
-        stv(a.Zh + off, xh);
-        stv(a.DZ + off, dz);
+        sts(a.Zh + off, xh, a.stream);
+        sts(a.DZ + off, dz, a.stream);
     }
 }
 
@@ -327,8 +358,8 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
                                               int q0, const T (&acc)[V], T uca, T ucb) {
     const size_t off = (size_t)row * a.ld + col0;
     T y[V], y0[V];
-    ldv(a.Z + off, y);
-    ldv(a.Z0 + off, y0);
+    lds(a.Z + off, y, a.stream);
+    lds(a.Z0 + off, y0, a.stream);
     const T lr = a.rlo[row], ur = a.rhi[row];
     T yh[V], yn[V], dz[V];
 #pragma unroll
@@ -344,14 +375,14 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
         // is, y^ - y = sigma (A xb - Pi(v)) without the cancellation of y
         dz[v] = p == s ? -y[v] : sg * (acc[v] - p);
     }
-    stv(a.Z + off, yn);
+    sts(a.Z + off, yn, a.stream);
     if (CHECK) {
         T dzp[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) dzp[v] = barrier(dz[v], lr, ur);
-        stv(a.Zh + off, yh);
-        stv(a.DZ + off, dz);
-        stv(a.Aux + off, dzp);
+        sts(a.Zh + off, yh, a.stream);
+        sts(a.DZ + off, dz, a.stream);
+        sts(a.Aux + off, dzp, a.stream);
     }
 }
 
@@ -607,10 +638,32 @@ cudaError_t dispatch_step(bool primal, bool check, const StepArgs<T>& a, int g_s
 
 }  // namespace
 
+// L2 bytes of the current device, looked up once per device
+static cudaError_t l2_bytes(long long* out) {
+    static std::atomic<long long> cache[kShapeDevices];  // static storage: starts at 0
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    long long v = dev >= 0 && dev < kShapeDevices ? cache[dev].load(std::memory_order_acquire) : 0;
+    if (v == 0) {
+        int b = 0;
+        if ((e = cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev)) != cudaSuccess) return e;
+        v = b > 0 ? b : 1;
+        if (dev >= 0 && dev < kShapeDevices) cache[dev].store(v, std::memory_order_release);
+    }
+    *out = v;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol, const T* hal, int t,
                              int ce, int uni, bool check, bool pdl, cudaStream_t s, cudaEvent_t* ev) {
     cudaError_t e;
+    long long l2 = 0;
+    if ((e = l2_bytes(&l2)) != cudaSuccess) return e;
+    // the gathered blocks: Y (m x ld) for the primal step, Xbar (n x ld) for the dual step
+    const long long ybytes = (long long)d.A.rows * ld * (long long)sizeof(T);
+    const long long xbytes = (long long)d.A.cols * ld * (long long)sizeof(T);
     StepArgs<T> p{};
     p.rows = d.At.rows;
     p.rp = d.At.rp;
@@ -644,6 +697,7 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     p.uni = uni;
     // the first primal step of an interval follows the check's copies
     p.pdl = pdl && t > 0 && !ev;
+    p.stream = 2 * ybytes > l2;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
     if ((e = dispatch_step<T>(true, check, p, d.At.g_shift, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
@@ -680,6 +734,7 @@ cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld,
     q.ce = ce;
     q.uni = uni;
     q.pdl = pdl && !ev;
+    q.stream = 2 * xbytes > l2;
     if ((e = dispatch_step<T>(false, check, q, d.A.g_shift, s)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
     return cudaSuccess;
