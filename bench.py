@@ -103,6 +103,13 @@ def golden_lps_and_ref(name, q):
     return list(range(q)), np.asarray(c["status"]), np.asarray(c["obj"]), None
 
 
+def golden_ref_tol(name):
+    c = golden_case(name)
+    if c is None:
+        return None
+    return c.get("ref_tol", c.get("tol"))
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -364,8 +371,10 @@ def oracle_error(w, name, batch, res):
     return {"lps": len(lps), "status_equal": int(np.sum(st == status)),
             "max_rel_obj_err": float(err.max()) if err.size else None,
             "max_oracle_rel_kkt": float(max(kkt)) if kkt else None, "kkt_lps": len(kkt),
-            "what": "against the FP64 oracle: reference objectives (rel-KKT 1e-6 or tighter) and the oracle's "
-                    "own KKT evaluation of the returned points, on the stored LPs of this batch"}
+            "ref_tol": golden_ref_tol(WORKLOADS[name]["golden"]),
+            "what": "against the FP64 oracle: statuses at this tolerance, reference objectives solved to ref_tol "
+                    "(or 1e-7 for whole batches), and the oracle's own KKT evaluation of the returned points, on "
+                    "the stored LPs of this batch"}
 
 
 def run_serving(args, rank, world, local):
