@@ -32,6 +32,7 @@
 // instantiated for float (mixed path), double (FP64 path) and dfloat (the
 // mixed path's polish phase: double-float values on the FP32 pipe).
 #include <atomic>
+#include <type_traits>
 
 #include "lpb_internal.h"
 
@@ -157,6 +158,16 @@ __device__ __forceinline__ dfloat mad(dfloat a, dfloat x, dfloat acc) { return d
 __device__ __forceinline__ float dot_acc(float a, float x, float acc) { return fmaf(a, x, acc); }
 __device__ __forceinline__ double dot_acc(double a, double x, double acc) { return fma(a, x, acc); }
 __device__ __forceinline__ dfloat dot_acc(dfloat a, dfloat x, dfloat acc) { return dfl_dot_acc(a, x, acc); }
+// 2 v, exact in every iterate type (for dfloat both parts scale)
+__device__ __forceinline__ float twice(float v) { return 2.0f * v; }
+__device__ __forceinline__ double twice(double v) { return 2.0 * v; }
+__device__ __forceinline__ dfloat twice(dfloat v) { return dfloat(2.0f * v.hi, 2.0f * v.lo); }
+// y / sigma: FP32 and FP64 divide; dfloat multiplies by the column's
+// reciprocal 1/sigma (staged once per block), which a double-float division
+// would recompute per element at several times the cost
+__device__ __forceinline__ float over_sigma(float y, float sg, float) { return y / sg; }
+__device__ __forceinline__ double over_sigma(double y, double sg, double) { return y / sg; }
+__device__ __forceinline__ dfloat over_sigma(dfloat y, dfloat, dfloat isg) { return y * isg; }
 template <int V> __device__ __forceinline__ void fin(float (&)[V]) {}
 template <int V> __device__ __forceinline__ void fin(double (&)[V]) {}
 template <int V> __device__ __forceinline__ void fin(dfloat (&acc)[V]) {
@@ -307,7 +318,7 @@ __device__ __forceinline__ T barrier(T v, T lo, T hi) {
 // ca, cb are the Halpern weights of the column's restart group
 template <typename T, int TN>
 struct TileParams {
-    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN], ca[TN], cb[TN], pa[TN], pb[TN];
+    T tau[TN], lo[TN], hi[TN], c[TN], sigma[TN], isigma[TN], ca[TN], cb[TN], pa[TN], pb[TN];
     int kind[TN], var[TN];
 };
 
@@ -339,7 +350,7 @@ __device__ __forceinline__ void primal_epilogue(const StepArgs<T>& a, const Tile
         s = s < hi ? s : hi;
         s = s > lo ? s : lo;
         xh[v] = s;
-        xb[v] = T(2) * s - x[v];
+        xb[v] = twice(s) - x[v];
         // x^ - x: where the box is not active it is -tau (c + G) exactly,
         // which stays accurate when |x| is large (diverging iterates of an
         // infeasible LP); elsewhere the difference with the bound
@@ -365,12 +376,12 @@ __device__ __forceinline__ void dual_epilogue(const StepArgs<T>& a, const TilePa
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const T sg = P.sigma[q0 + v];
-        const T s = y[v] / sg + acc[v];
+        const T s = over_sigma(y[v], sg, P.isigma[q0 + v]) + acc[v];
         T p = s < ur ? s : ur;
         p = p > lr ? p : lr;
         yh[v] = sg * (s - p);
         const T ca = a.uni >= 0 ? uca : P.ca[q0 + v], cb = a.uni >= 0 ? ucb : P.cb[q0 + v];
-        yn[v] = ca * (T(2) * yh[v] - y[v]) + cb * y0[v];
+        yn[v] = ca * (twice(yh[v]) - y[v]) + cb * y0[v];
         // y^ - y: y^ = 0 exactly where the row bound is not active; where it
         // is, y^ - y = sigma (A xb - Pi(v)) without the cancellation of y
         dz[v] = p == s ? -y[v] : sg * (acc[v] - p);
@@ -454,6 +465,7 @@ __global__ void __launch_bounds__(kBlock, (MinBlocks<T, G, PRIMAL>::v)) k_step(c
             P.c[q] = in ? a.col.c[j] : T(0);
         } else {
             P.sigma[q] = in ? a.col.sigma[j] : T(1);
+            if (std::is_same<T, dfloat>::value) P.isigma[q] = T(1) / P.sigma[q];
         }
     }
     __syncthreads();
