@@ -183,6 +183,32 @@ lpb_err lpb_solve_dev(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs_de
                       int64_t max_iter, const double* warm_x_dev, const double* warm_y_dev,
                       lpb_batch_t* out);
 
+/* Most handles in one lpb_solve_multi call. */
+enum { LPB_MAX_JOINT = 64 };
+
+/* Solves count batches on count different handles together (Sec. 5, the
+ * batched iteration of Eq. batched_iter, run over LPs of several matrices,
+ * i.e. LPs of uneven size and iteration count in one launch).  Batch i is
+ * num_lps[i] LPs of handles[i] with the host override records specs[i]
+ * (as lpb_solve, no warm start).  Every iteration runs the primal steps of
+ * all batches still iterating as one kernel launch, then their dual steps
+ * as one launch (one launch per row-group width among the batches and per
+ * 8 batches), and each batch's check after the interval, all on the first
+ * handle's stream; with the first handle's use_graphs each interval is one
+ * CUDA graph.  A batch that finishes leaves the joint launches; one that
+ * stalls at FP32 resolution (LPB_MIXED with fp64_polish) leaves them and is
+ * polished on its own handle and stream.  Each result is bitwise the one
+ * lpb_solve gives for that batch alone.  Event timing (profile = 1) is not
+ * taken; each batch's lpb_profile counts its share of the launches as if
+ * solved alone.
+ * Rejects (LPB_ERR_INVALID_ARG): count outside [1, LPB_MAX_JOINT], a NULL
+ * array, a handle twice, handles on different devices or with different
+ * precision or check_every, and whatever lpb_solve rejects for a batch.
+ * On LPB_OK out[i] owns batch i's results until lpb_batch_free; on an error
+ * every out[i] is NULL. */
+lpb_err lpb_solve_multi(int32_t count, const lpb_handle* handles, const int32_t* num_lps,
+                        const lpb_lp_spec* const* specs, double tol, int64_t max_iter, lpb_batch_t* out);
+
 /* Result of LP lp of a batch: *res, and optionally x (n doubles) and y (m
  * doubles) in the original, unscaled space (x = D_c x~, y = D_r y~). */
 lpb_err lpb_result(lpb_batch_t b, int32_t lp, lpb_lp_result* res, double* x, double* y);

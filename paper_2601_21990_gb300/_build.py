@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "lpb")
 LIB = os.path.join(PKG, "liblpb.so")
-SOURCES = ["lpb_api.cu", "lpb_engine.cu", "lpb_serve.cu", "lpb_setup.cu", "lpb_iter.cu", "lpb_check.cu", "lpb_noalloc.cu"]
+SOURCES = ["lpb_api.cu", "lpb_engine.cu", "lpb_serve.cu", "lpb_setup.cu", "lpb_iter.cu", "lpb_multi.cu", "lpb_check.cu",
+           "lpb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -89,11 +89,43 @@ lpb_err run_group(lpb_ctx* h, Lane& ln, GroupRun& g, std::vector<GroupRun*>& gro
         if ((rc = lane_interval<T>(h, ln, L, stall_checks, s, &prof)) != LPB_OK) return rc;
         CU(cudaStreamSynchronize(s));
         add_interval_times(h, L, &prof);
-        if ((rc = lane_collect<T>(h, ln, groups, s, &prof)) != LPB_OK) return rc;
+        if ((rc = lane_collect<T>(h, ln, groups, s, &prof, true)) != LPB_OK) return rc;
         if (can_stall && g.live > 0 && g.stalled) return LPB_OK;
     }
     done = true;
     return LPB_OK;
+}
+
+// Polish: group g, stalled on the handle's FP32 lane ln, continues from its
+// FP32 state in double-float (or FP64) iterates on the polish lane, with its
+// restart state (k, r0, w, ...) carried over.
+lpb_err polish_group(lpb_ctx* h, Lane& ln, GroupRun& g, std::vector<GroupRun*>& groups, lpb_profile& prof) {
+    cudaStream_t s = h->stream;
+    const int pp = polish_dfloat(h) ? kPrecDfl : kPrecF64;
+    Lane& pl = h->lane[pp];
+    std::vector<GroupRun*> pgroups(1, nullptr);
+    prof.kernels += 5;
+    prof.fp64_switch_iter = g.K;
+    bool done = true;
+    lpb_err rc = lane_reserve(h, pl, pp, ln.cap, 1);
+    if (rc == LPB_OK) {
+        if (pp == kPrecDfl) {
+            if ((rc = lane_migrate<dfloat>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
+                pgroups[0] = &g;
+                rc = run_group<dfloat>(h, pl, g, pgroups, false, done, prof);
+            }
+        } else {
+            if ((rc = lane_migrate<double>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
+                pgroups[0] = &g;
+                rc = run_group<double>(h, pl, g, pgroups, false, done, prof);
+            }
+        }
+    }
+    if (rc != LPB_OK) {
+        pl.ncol = 0;
+        cudaMemsetAsync(pl.ctl, 0, sizeof(Control) * pl.gcap, s);
+    }
+    return rc;
 }
 
 // A batched solve: the batch is one restart group on the handle's lane of
@@ -134,32 +166,7 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
     bool done = true;
     const bool can_stall = std::is_same<T, float>::value && polish_enabled(h);
     if (rc == LPB_OK && g.live > 0) rc = run_group<T>(h, ln, g, groups, can_stall, done, prof);
-    if (rc == LPB_OK && !done) {
-        // polish: the group continues from its FP32 state in double-float (or
-        // FP64) iterates with its restart state (k, r0, w, ...) carried over
-        const int pp = polish_dfloat(h) ? kPrecDfl : kPrecF64;
-        Lane& pl = h->lane[pp];
-        std::vector<GroupRun*> pgroups(1, nullptr);
-        prof.kernels += 5;
-        prof.fp64_switch_iter = g.K;
-        if ((rc = lane_reserve(h, pl, pp, ln.cap, 1)) == LPB_OK) {
-            if (pp == kPrecDfl) {
-                if ((rc = lane_migrate<dfloat>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
-                    pgroups[0] = &g;
-                    rc = run_group<dfloat>(h, pl, g, pgroups, false, done, prof);
-                }
-            } else {
-                if ((rc = lane_migrate<double>(h, ln, pl, g, 0, 0, s, groups)) == LPB_OK) {
-                    pgroups[0] = &g;
-                    rc = run_group<double>(h, pl, g, pgroups, false, done, prof);
-                }
-            }
-        }
-        if (rc != LPB_OK) {
-            pl.ncol = 0;
-            cudaMemsetAsync(pl.ctl, 0, sizeof(Control) * pl.gcap, s);
-        }
-    }
+    if (rc == LPB_OK && !done) rc = polish_group(h, ln, g, groups, prof);
     if (rc != LPB_OK) {
         // leave the lane empty for the next solve
         ln.ncol = 0;
@@ -170,6 +177,109 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
     }
     CU(cudaStreamSynchronize(s));
     return LPB_OK;
+}
+
+// A joint solve: batch i is one restart group on the lane of handle hs[i]
+// (specs_dev[i] on that handle's device memory).  The lanes step together,
+// one joint interval after another on the first handle's stream, until
+// every batch is done or has stalled at FP32 resolution; a stalled batch
+// then polishes alone on its own handle.
+template <typename T>
+lpb_err solve_joint_impl(const std::vector<lpb_ctx*>& hs, const int32_t* num_lps,
+                         const std::vector<const lpb_lp_spec*>& specs_dev, double tol, int64_t max_iter,
+                         std::vector<lpb_batch*>& bts) {
+    const int count = (int)hs.size(), prec = prec_of<T>();
+    cudaStream_t s = hs[0]->stream;
+    std::vector<GroupRun> g(count);
+    std::vector<std::vector<GroupRun*>> groups(count, std::vector<GroupRun*>(1, nullptr));
+    std::vector<char> can_stall(count, 0), admitted(count, 0);
+    lpb_err rc = LPB_OK;
+    for (int i = 0; i < count && rc == LPB_OK; ++i) {
+        lpb_ctx* h = hs[i];
+        Lane& ln = h->lane[prec];
+        lpb_batch* bt = bts[i];
+        const int nl = num_lps[i], n = h->n, m = h->m;
+        if ((rc = lane_reserve(h, ln, prec, nl, 1)) != LPB_OK) break;
+        if ((rc = ensure_check_ws(h, ln.cap)) != LPB_OK) break;
+        cudaError_t e = cudaMalloc((void**)&bt->x, sizeof(double) * (size_t)n * (nl ? nl : 1));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&bt->y, sizeof(double) * (size_t)(m ? m : 1) * (nl ? nl : 1));
+        if (e == cudaSuccess) e = cudaMemsetAsync(bt->x, 0, sizeof(double) * (size_t)n * nl, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bt->y, 0, sizeof(double) * (size_t)m * nl, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "joint solve: result buffers");
+            break;
+        }
+        bt->res.assign(nl, lpb_lp_result{});
+        bt->prof.setup_ms = h->setup_ms;
+        bt->prof.fp64_switch_iter = -1;
+        if (nl == 0) continue;
+        GroupRun& gi = g[i];
+        gi.id = 0;
+        gi.count = nl;
+        gi.slot0 = 0;
+        gi.max_iter = max_iter;
+        gi.res = bt->res.data();
+        gi.x_dev = bt->x;
+        gi.y_dev = bt->y;
+        bt->prof.kernels += 3;
+        admitted[i] = 1;
+        rc = lane_admit<T>(h, ln, gi, specs_dev[i], nullptr, nullptr, n, m, tol, h->stream, groups[i]);
+        can_stall[i] = std::is_same<T, float>::value && polish_enabled(h);
+    }
+    JointGraph jg;
+    std::vector<int> act;
+    std::vector<lpb_ctx*> ah;
+    std::vector<Lane*> al;
+    std::vector<int> sc;
+    std::vector<lpb_profile*> ap;
+    while (rc == LPB_OK) {
+        act.clear();
+        for (int i = 0; i < count; ++i)
+            if (g[i].live > 0 && !(can_stall[i] && g[i].stalled)) act.push_back(i);
+        if (act.empty()) break;
+        // the active groups started together and ran the same intervals: one K
+        const int L = (int)std::min<int64_t>(hs[act[0]]->opt.check_every, max_iter - g[act[0]].K);
+        ah.clear();
+        al.clear();
+        sc.clear();
+        ap.clear();
+        for (int i : act) {
+            ah.push_back(hs[i]);
+            al.push_back(&hs[i]->lane[prec]);
+            sc.push_back(can_stall[i] ? hs[i]->opt.polish_stall_checks : 0);
+            ap.push_back(&bts[i]->prof);
+        }
+        if ((rc = joint_interval<T>(ah.data(), al.data(), sc.data(), (int)act.size(), L, s, jg, ap.data())) != LPB_OK)
+            break;
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "joint solve: interval");
+            break;
+        }
+        for (int i : act)
+            if ((rc = lane_collect<T>(hs[i], hs[i]->lane[prec], groups[i], s, &bts[i]->prof, true)) != LPB_OK) break;
+    }
+    joint_graph_free(jg);
+    if (rc == LPB_OK) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "joint solve");
+    }
+    for (int i = 0; i < count && rc == LPB_OK; ++i)
+        if (g[i].live > 0) rc = polish_group(hs[i], hs[i]->lane[prec], g[i], groups[i], bts[i]->prof);
+    for (int i = 0; i < count; ++i) {
+        lpb_ctx* h = hs[i];
+        Lane& ln = h->lane[prec];
+        if (rc != LPB_OK && admitted[i]) {
+            // leave the lane empty for the next solve
+            ln.ncol = 0;
+            std::fill(ln.slot_used.begin(), ln.slot_used.end(), 0);
+            cudaMemsetAsync(ln.ctl, 0, sizeof(Control) * ln.gcap, h->stream);
+        }
+        const cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (rc == LPB_OK && e != cudaSuccess) rc = cuda_fail(e, "joint solve");
+    }
+    return rc;
 }
 
 // Times R plain iterations (no check) of `count` copies of the base LP on the
@@ -278,6 +388,20 @@ lpb_err check_solve_args(lpb_handle h, int32_t num_lps, const void* specs, doubl
     if (num_lps > 0 && !specs) return fail(LPB_ERR_INVALID_ARG, "specs is NULL");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(LPB_ERR_INVALID_ARG, "tol must be positive and finite");
     if (max_iter < 1) return fail(LPB_ERR_INVALID_ARG, "max_iter must be >= 1");
+    return LPB_OK;
+}
+
+// host override records: kinds, variable indices, bounds and signs
+lpb_err check_specs(const lpb_ctx* h, int32_t num_lps, const lpb_lp_spec* specs) {
+    for (int32_t q = 0; q < num_lps; ++q) {
+        const lpb_lp_spec& sp = specs[q];
+        if (sp.kind < 0 || sp.kind > 2) return fail(LPB_ERR_INVALID_ARG, "override kind must be 0, 1 or 2");
+        if (sp.kind != 0 && (sp.var < 0 || sp.var >= h->n))
+            return fail(LPB_ERR_BAD_INDEX, "an override names a variable outside [0, n)");
+        if (sp.kind == 1 && (std::isnan(sp.lo) || std::isnan(sp.hi)))
+            return fail(LPB_ERR_INVALID_ARG, "NaN override bound");
+        if (sp.kind == 2 && !std::isfinite(sp.sign)) return fail(LPB_ERR_INVALID_ARG, "non-finite objective sign");
+    }
     return LPB_OK;
 }
 
@@ -542,15 +666,7 @@ lpb_err lpb_solve(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs, doubl
     lpb_err rc = check_solve_args(h, num_lps, specs, tol, max_iter, out);
     if (rc != LPB_OK) return rc;
     *out = nullptr;
-    for (int32_t q = 0; q < num_lps; ++q) {
-        const lpb_lp_spec& sp = specs[q];
-        if (sp.kind < 0 || sp.kind > 2) return fail(LPB_ERR_INVALID_ARG, "override kind must be 0, 1 or 2");
-        if (sp.kind != 0 && (sp.var < 0 || sp.var >= h->n))
-            return fail(LPB_ERR_BAD_INDEX, "an override names a variable outside [0, n)");
-        if (sp.kind == 1 && (std::isnan(sp.lo) || std::isnan(sp.hi)))
-            return fail(LPB_ERR_INVALID_ARG, "NaN override bound");
-        if (sp.kind == 2 && !std::isfinite(sp.sign)) return fail(LPB_ERR_INVALID_ARG, "non-finite objective sign");
-    }
+    if ((rc = check_specs(h, num_lps, specs)) != LPB_OK) return rc;
     DeviceGuard guard(h->device);
     if ((rc = ensure_specs(h, num_lps)) != LPB_OK) return rc;
     cudaStream_t s = h->stream;
@@ -577,6 +693,56 @@ lpb_err lpb_solve_dev(lpb_handle h, int32_t num_lps, const lpb_lp_spec* specs_de
     *out = nullptr;
     DeviceGuard guard(h->device);
     return solve_common(h, num_lps, specs_dev, tol, max_iter, warm_x_dev, h->m > 0 ? warm_y_dev : nullptr, out);
+}
+
+lpb_err lpb_solve_multi(int32_t count, const lpb_handle* handles, const int32_t* num_lps,
+                        const lpb_lp_spec* const* specs, double tol, int64_t max_iter, lpb_batch_t* out) {
+    if (!handles || !num_lps || !specs || !out) return fail(LPB_ERR_INVALID_ARG, "null argument");
+    if (count < 1 || count > LPB_MAX_JOINT) return fail(LPB_ERR_INVALID_ARG, "count must be in [1, LPB_MAX_JOINT]");
+    for (int32_t i = 0; i < count; ++i) out[i] = nullptr;
+    std::vector<lpb_ctx*> hs(count);
+    lpb_err rc;
+    for (int32_t i = 0; i < count; ++i) {
+        if ((rc = check_solve_args(handles[i], num_lps[i], specs[i], tol, max_iter, out + i)) != LPB_OK) return rc;
+        hs[i] = handles[i];
+        for (int32_t j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(LPB_ERR_INVALID_ARG, "a handle appears twice in a joint solve");
+        if (hs[i]->device != hs[0]->device) return fail(LPB_ERR_INVALID_ARG, "joint solve handles on different devices");
+        if (hs[i]->opt.precision != hs[0]->opt.precision)
+            return fail(LPB_ERR_INVALID_ARG, "joint solve handles with different precisions");
+        if (hs[i]->opt.check_every != hs[0]->opt.check_every)
+            return fail(LPB_ERR_INVALID_ARG, "joint solve handles with different check_every");
+        if ((rc = check_specs(hs[i], num_lps[i], specs[i])) != LPB_OK) return rc;
+    }
+    DeviceGuard guard(hs[0]->device);
+    std::vector<const lpb_lp_spec*> sd(count, nullptr);
+    for (int32_t i = 0; i < count; ++i) {
+        if ((rc = ensure_specs(hs[i], num_lps[i])) != LPB_OK) return rc;
+        if (num_lps[i] > 0)
+            CU(cudaMemcpyAsync(hs[i]->specs_dev, specs[i], sizeof(lpb_lp_spec) * num_lps[i], cudaMemcpyHostToDevice,
+                               hs[i]->stream));
+        sd[i] = hs[i]->specs_dev;
+    }
+    std::vector<lpb_batch*> bts(count, nullptr);
+    for (int32_t i = 0; i < count; ++i) {
+        bts[i] = new (std::nothrow) lpb_batch();
+        if (!bts[i]) {
+            for (lpb_batch* b : bts) lpb_batch_free(b);
+            return fail(LPB_ERR_OOM, "host allocation failed");
+        }
+        bts[i]->device = hs[i]->device;
+        bts[i]->num_lps = num_lps[i];
+        bts[i]->m = hs[i]->m;
+        bts[i]->n = hs[i]->n;
+    }
+    rc = hs[0]->opt.precision == LPB_MIXED ? solve_joint_impl<float>(hs, num_lps, sd, tol, max_iter, bts)
+                                           : solve_joint_impl<double>(hs, num_lps, sd, tol, max_iter, bts);
+    if (rc != LPB_OK) {
+        for (lpb_batch* b : bts) lpb_batch_free(b);
+        return rc;
+    }
+    for (int32_t i = 0; i < count; ++i) out[i] = bts[i];
+    return LPB_OK;
 }
 
 lpb_err lpb_result(lpb_batch_t b, int32_t lp, lpb_lp_result* res, double* x, double* y) {

@@ -88,11 +88,14 @@ void set_result(lpb_lp_result& r, const ColRecord& rc, int status, int64_t iters
 
 // Removes the columns `gone` (ascending) from the lane by moving live tail
 // columns into their places; the moves run on the device.
+// idle: the caller has synchronized s since it last queued copies from the
+// lane's pinned move lists.
 template <typename T>
-lpb_err compact(lpb_ctx* h, Lane& ln, const std::vector<int>& gone, cudaStream_t s, lpb_profile* prof) {
+lpb_err compact(lpb_ctx* h, Lane& ln, const std::vector<int>& gone, cudaStream_t s, lpb_profile* prof,
+                bool idle = false) {
     if (gone.empty()) return LPB_OK;
     // the pinned move lists may still be read by copies queued earlier
-    LPB_CU(cudaStreamSynchronize(s));
+    if (!idle) LPB_CU(cudaStreamSynchronize(s));
     const int ncol = ln.ncol;
     std::vector<char> is_gone(ncol, 0);
     for (int f : gone) is_gone[f] = 1;
@@ -436,33 +439,103 @@ lpb_err lane_admit(lpb_ctx* h, Lane& ln, GroupRun& g, const lpb_lp_spec* specs_d
     return LPB_OK;
 }
 
-// The work of one interval queued on stream s: L iterations, the check, the
-// copies of the per-column and per-group records.
+namespace {
+
+// The check of lane ln after an interval of L iterations, then the copies
+// of the per-column and per-group records to their pinned mirrors.
 template <typename T>
-lpb_err queue_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, int uni, bool timed, cudaStream_t s) {
-    const int ld = ln.cap, ce = h->opt.check_every;
-    const IterData<T> id = iter_data<T>(h, ln);
-    const IterBufs<T> ib = iter_bufs<T>(ln);
+lpb_err queue_check(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, cudaEvent_t* ev) {
     const CheckData cd = lane_check_data(h, ln, stall_checks);
-    const T* hal = pick<T>(ln.hal64, ln.hal32, ln.haldf);
-    const bool pdl = h->opt.use_pdl != 0;
-    for (int t = 0; t < L; ++t)
-        LPB_CU(launch_iteration<T>(id, ib, ld, ln.ncol, hal, t, ce, uni, t == L - 1, pdl, s,
-                                   timed ? &h->events[3 * t] : nullptr));
-    LPB_CU(launch_check<T>(cd, ib, ld, ln.ncol, L, h->P, h->Q, h->partials, h->colsum, ln.rec, id.col, s,
-                           timed ? &h->events[3 * L] : nullptr));
+    LPB_CU(launch_check<T>(cd, iter_bufs<T>(ln), ln.cap, ln.ncol, L, h->P, h->Q, h->partials, h->colsum, ln.rec,
+                           iter_data<T>(h, ln).col, s, ev));
     LPB_CU(cudaMemcpyAsync(ln.rec_h, ln.rec, sizeof(ColRecord) * ln.ncol, cudaMemcpyDeviceToHost, s));
     LPB_CU(cudaMemcpyAsync(ln.ctl_h, ln.ctl, sizeof(Control) * ln.gcap, cudaMemcpyDeviceToHost, s));
     return LPB_OK;
 }
 
+// Queues the L iterations of an interval, the check and the copies of the
+// per-column and per-group records.
 template <typename T>
-lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, lpb_profile* prof) {
-    const int m = h->m, ce = h->opt.check_every;
-    const bool timed = prof && h->opt.profile && (int)h->events.size() >= 3 * ce + 3;
+lpb_err queue_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, int uni, bool timed, cudaStream_t s) {
+    const int ld = ln.cap, ce = h->opt.check_every;
+    const IterData<T> id = iter_data<T>(h, ln);
+    const IterBufs<T> ib = iter_bufs<T>(ln);
+    const T* hal = pick<T>(ln.hal64, ln.hal32, ln.haldf);
+    const bool pdl = h->opt.use_pdl != 0;
+    for (int t = 0; t < L; ++t)
+        LPB_CU(launch_iteration<T>(id, ib, ld, ln.ncol, hal, t, ce, uni, t == L - 1, pdl, s,
+                                   timed ? &h->events[3 * t] : nullptr));
+    return queue_check<T>(h, ln, L, stall_checks, s, timed ? &h->events[3 * L] : nullptr);
+}
+
+// the group of every active column of the lane, or -1
+int lane_uni(const Lane& ln) {
     int uni = ln.ncol > 0 ? ln.col_group[0] : -1;
     for (int j = 1; j < ln.ncol && uni >= 0; ++j)
         if (ln.col_group[j] != uni) uni = -1;
+    return uni;
+}
+
+// Captures what queue() puts on stream s as a CUDA graph and makes *exec
+// replay it: updated in place when the topology allows, else instantiated
+// anew.
+template <typename Q>
+lpb_err capture_into(cudaGraphExec_t* exec, cudaStream_t s, Q queue) {
+    cudaGraph_t g = nullptr;
+    LPB_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const lpb_err rc = queue();
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != LPB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    LPB_CU(e);
+    if (*exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(*exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(*exec);
+            *exec = nullptr;
+        }
+    }
+    if (!*exec) {
+        const cudaError_t ei = cudaGraphInstantiate(exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            *exec = nullptr;
+            return cuda_fail(ei, "cudaGraphInstantiate");
+        }
+    }
+    cudaGraphDestroy(g);
+    return LPB_OK;
+}
+
+// launches, kernels and algorithmic bytes of one interval of lane ln
+template <typename T>
+void count_interval(const lpb_ctx* h, const Lane& ln, int L, lpb_profile* prof) {
+    if (!prof) return;
+    const int m = h->m;
+    for (int t = 0; t < L; ++t) {
+        const bool chk = t == L - 1;
+        prof->launches[0] += 1;
+        prof->launches[1] += m > 0 ? 1 : 0;
+        prof->kernels += m > 0 ? 2 : 1;
+        prof->bytes[0] += step_bytes(prec_of<T>(), h->nnz, m, h->n, true, chk, ln.ncol);
+        prof->bytes[1] += step_bytes(prec_of<T>(), h->nnz, m, h->n, false, chk, ln.ncol);
+    }
+    prof->launches[2] += m > 0 ? 2 : 1;
+    prof->launches[3] += 1;
+    prof->checks += 1;
+    prof->kernels += (m > 0 ? 2 : 1) + (m > 0 ? 1 : 0) + 1 + 1 + 1 + (m > 0 ? 2 : 1);
+}
+
+}  // namespace
+
+template <typename T>
+lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, lpb_profile* prof) {
+    const int ce = h->opt.check_every;
+    const bool timed = prof && h->opt.profile && (int)h->events.size() >= 3 * ce + 3;
+    const int uni = lane_uni(ln);
     if (!h->opt.use_graphs || timed) {
         lpb_err rc = queue_interval<T>(h, ln, L, stall_checks, uni, timed, s);
         if (rc != LPB_OK) return rc;
@@ -471,57 +544,75 @@ lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_
         // a new shape updates the executable graph in place when it can
         const GraphKey key = interval_key(h, ln, L, stall_checks, uni, (int)sizeof(T));
         if (!ln.exec || !(ln.gkey == key)) {
-            cudaGraph_t g = nullptr;
-            LPB_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            const lpb_err rc = queue_interval<T>(h, ln, L, stall_checks, uni, false, s);
-            const cudaError_t e = cudaStreamEndCapture(s, &g);
-            if (rc != LPB_OK) {
-                if (g) cudaGraphDestroy(g);
-                return rc;
-            }
-            LPB_CU(e);
-            if (ln.exec) {
-                cudaGraphExecUpdateResultInfo info{};
-                if (cudaGraphExecUpdate(ln.exec, g, &info) != cudaSuccess) {
-                    cudaGetLastError();
-                    cudaGraphExecDestroy(ln.exec);
-                    ln.exec = nullptr;
-                }
-            }
-            if (!ln.exec) {
-                const cudaError_t ei = cudaGraphInstantiate(&ln.exec, g, 0);
-                if (ei != cudaSuccess) {
-                    cudaGraphDestroy(g);
-                    ln.exec = nullptr;
-                    return cuda_fail(ei, "cudaGraphInstantiate");
-                }
-            }
-            cudaGraphDestroy(g);
+            const lpb_err rc = capture_into(&ln.exec, s, [&] { return queue_interval<T>(h, ln, L, stall_checks, uni, false, s); });
+            if (rc != LPB_OK) return rc;
             ln.gkey = key;
         }
         LPB_CU(cudaGraphLaunch(ln.exec, s));
     }
-    for (int t = 0; t < L; ++t) {
-        const bool chk = t == L - 1;
-        if (prof) {
-            prof->launches[0] += 1;
-            prof->launches[1] += m > 0 ? 1 : 0;
-            prof->kernels += m > 0 ? 2 : 1;
-            prof->bytes[0] += step_bytes(prec_of<T>(), h->nnz, m, h->n, true, chk, ln.ncol);
-            prof->bytes[1] += step_bytes(prec_of<T>(), h->nnz, m, h->n, false, chk, ln.ncol);
+    count_interval<T>(h, ln, L, prof);
+    return LPB_OK;
+}
+
+void joint_graph_free(JointGraph& jg) {
+    if (jg.exec) cudaGraphExecDestroy(jg.exec);
+    jg.exec = nullptr;
+    jg.keys.clear();
+    jg.seen.clear();
+}
+
+template <typename T>
+lpb_err joint_interval(lpb_ctx* const* hs, Lane* const* lns, const int* stall_checks, int count, int L,
+                       cudaStream_t s, JointGraph& jg, lpb_profile* const* profs) {
+    std::vector<IterPart<T>> parts(count);
+    std::vector<GraphKey> keys(count);
+    for (int i = 0; i < count; ++i) {
+        const lpb_ctx* h = hs[i];
+        const Lane& ln = *lns[i];
+        IterPart<T>& q = parts[i];
+        q.d = iter_data<T>(h, ln);
+        q.b = iter_bufs<T>(ln);
+        q.ld = ln.cap;
+        q.ncol = ln.ncol;
+        q.ce = h->opt.check_every;
+        q.uni = lane_uni(ln);
+        q.hal = pick<T>(ln.hal64, ln.hal32, ln.haldf);
+        keys[i] = interval_key(h, ln, L, stall_checks[i], q.uni, (int)sizeof(T));
+    }
+    const bool pdl = hs[0]->opt.use_pdl != 0;
+    auto queue = [&]() -> lpb_err {
+        for (int t = 0; t < L; ++t) LPB_CU(launch_iteration_multi<T>(parts.data(), count, t, t == L - 1, pdl, s));
+        for (int i = 0; i < count; ++i) {
+            const lpb_err rc = queue_check<T>(hs[i], *lns[i], L, stall_checks[i], s, nullptr);
+            if (rc != LPB_OK) return rc;
         }
+        return LPB_OK;
+    };
+    // one graph per joint shape (every lane's interval key, in order), taken
+    // once the shape has held for an interval: with several lanes some lane
+    // compacts at most checks, and a graph replayed once does not repay its
+    // capture
+    const bool replay = hs[0]->opt.use_graphs && jg.exec && jg.keys == keys;
+    const bool capture = hs[0]->opt.use_graphs && !replay && jg.seen == keys;
+    if (replay || capture) {
+        if (capture) {
+            const lpb_err rc = capture_into(&jg.exec, s, queue);
+            if (rc != LPB_OK) return rc;
+            jg.keys = keys;
+        }
+        LPB_CU(cudaGraphLaunch(jg.exec, s));
+    } else {
+        const lpb_err rc = queue();
+        if (rc != LPB_OK) return rc;
     }
-    if (prof) {
-        prof->launches[2] += m > 0 ? 2 : 1;
-        prof->launches[3] += 1;
-        prof->checks += 1;
-        prof->kernels += (m > 0 ? 2 : 1) + (m > 0 ? 1 : 0) + 1 + 1 + 1 + (m > 0 ? 2 : 1);
-    }
+    jg.seen = keys;
+    for (int i = 0; i < count; ++i) count_interval<T>(hs[i], *lns[i], L, profs ? profs[i] : nullptr);
     return LPB_OK;
 }
 
 template <typename T>
-lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaStream_t s, lpb_profile* prof) {
+lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaStream_t s, lpb_profile* prof,
+                     bool idle) {
     for (int gi = 0; gi < (int)groups.size(); ++gi) {
         GroupRun* g = groups[gi];
         if (!g) continue;
@@ -542,7 +633,7 @@ lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaS
     }
     if (fin.empty()) return LPB_OK;
     const int cnt = (int)fin.size();
-    LPB_CU(cudaStreamSynchronize(s));  // pinned lists free for reuse
+    if (!idle) LPB_CU(cudaStreamSynchronize(s));  // pinned lists free for reuse
     int* cols = ln.mv_h + 2 * ln.cap;
     for (int f = 0; f < cnt; ++f) {
         const int j = fin[f];
@@ -565,7 +656,9 @@ lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaS
             std::find(done_groups.begin(), done_groups.end(), gi) == done_groups.end())
             done_groups.push_back(gi);
     }
-    lpb_err rc = compact<T>(h, ln, fin, s, prof);
+    // the extraction's copies read the column and pointer lists, not the
+    // move lists that the compaction fills
+    lpb_err rc = compact<T>(h, ln, fin, s, prof, idle);
     if (rc != LPB_OK) return rc;
     for (int gi : done_groups) {
         if ((rc = retire_group(ln, *groups[gi], s)) != LPB_OK) return rc;
@@ -627,13 +720,17 @@ template <typename T> const T* lane_hal(const Lane& ln) { return pick<T>(ln.hal6
     template lpb_err lane_admit<T>(lpb_ctx*, Lane&, GroupRun&, const lpb_lp_spec*, const double*, const double*,  \
                                    int64_t, int64_t, double, cudaStream_t, std::vector<GroupRun*>&);               \
     template lpb_err lane_interval<T>(lpb_ctx*, Lane&, int, int, cudaStream_t, lpb_profile*);                      \
-    template lpb_err lane_collect<T>(lpb_ctx*, Lane&, std::vector<GroupRun*>&, cudaStream_t, lpb_profile*);          \
+    template lpb_err lane_collect<T>(lpb_ctx*, Lane&, std::vector<GroupRun*>&, cudaStream_t, lpb_profile*, bool);    \
     template IterData<T> lane_iter_data<T>(const lpb_ctx*, const Lane&);                                            \
     template IterBufs<T> lane_iter_bufs<T>(const Lane&);                                                            \
     template const T* lane_hal<T>(const Lane&);
 LPB_ENGINE_INSTANTIATE(float)
 LPB_ENGINE_INSTANTIATE(double)
 LPB_ENGINE_INSTANTIATE(dfloat)
+template lpb_err joint_interval<float>(lpb_ctx* const*, Lane* const*, const int*, int, int, cudaStream_t,
+                                       JointGraph&, lpb_profile* const*);
+template lpb_err joint_interval<double>(lpb_ctx* const*, Lane* const*, const int*, int, int, cudaStream_t,
+                                        JointGraph&, lpb_profile* const*);
 template lpb_err lane_migrate<double>(lpb_ctx*, Lane&, Lane&, GroupRun&, int, int, cudaStream_t,
                                       std::vector<GroupRun*>&);
 template lpb_err lane_migrate<dfloat>(lpb_ctx*, Lane&, Lane&, GroupRun&, int, int, cudaStream_t,

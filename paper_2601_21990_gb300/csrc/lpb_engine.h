@@ -191,11 +191,33 @@ lpb_err lane_admit(lpb_ctx* h, Lane& ln, GroupRun& g, const lpb_lp_spec* specs_d
 template <typename T>
 lpb_err lane_interval(lpb_ctx* h, Lane& ln, int L, int stall_checks, cudaStream_t s, lpb_profile* prof);
 
+// A joint interval's executable graph and the interval keys of its lanes,
+// in order, and the keys of the last interval run; owned by the joint solve.
+struct JointGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<GraphKey> keys, seen;
+};
+void joint_graph_free(JointGraph& jg);
+
+// One interval of the lanes lns[0 .. count) of several handles at once (one
+// iterate type, the same check interval), all on stream s: L iterations
+// whose primal and dual steps each run as one launch over every lane
+// (launch_iteration_multi), then each lane's check and record copies.  With
+// the first handle's use_graphs it is one CUDA graph in jg, replayed while
+// every lane's interval key holds (captured once a shape has held for one
+// interval).  Each lane's results are those of lane_interval on its own.
+template <typename T>
+lpb_err joint_interval(lpb_ctx* const* hs, Lane* const* lns, const int* stall_checks, int count, int L,
+                       cudaStream_t s, JointGraph& jg, lpb_profile* const* profs);
+
 // After the interval's stream work is done: statuses of the checked
 // columns, results and extraction of the finished ones, compaction, group
 // progress (K, stalls).  groups[id] is the host record of group id.
+// idle: s has been synchronized since the lane's last interval, so no copy
+// queued earlier still reads its pinned lists (saves two waits).
 template <typename T>
-lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaStream_t s, lpb_profile* prof);
+lpb_err lane_collect(lpb_ctx* h, Lane& ln, std::vector<GroupRun*>& groups, cudaStream_t s, lpb_profile* prof,
+                     bool idle = false);
 
 // Moves group g (all of its live columns) from the FP32 lane src to the
 // polish lane dst (precision TD), into columns [dst.ncol, ...) as group

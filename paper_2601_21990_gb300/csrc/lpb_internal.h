@@ -202,16 +202,42 @@ struct IterData {
 // One reflected-Halpern PDHG iteration on columns [0, ncol): primal step
 // (A~^T Y fused with the box projection, reflection and Halpern update) then
 // dual step (A~ Xbar fused with the row projection and Halpern update).
-// hal[2 (g ce + t)], hal[2 (g ce + t) + 1] are the Halpern weights
-// (k+1)/(k+2), 1/(k+2) of Eq. mainiter for iteration t of the interval of
-// restart group g (ce = check_every), written on the device by the checks.
-// uni >= 0 says that every active column belongs to group uni.  With pdl
-// the step kernels after the interval's first are programmatic dependents of
-// their predecessor (not with timing events, which sit between them).
+// hal[2 (g (ce + 1) + e)], hal[2 (g (ce + 1) + e) + 1] are the Halpern
+// weights (k+1)/(k+2), 1/(k+2) of Eq. mainiter for k = k_start - 1 + e of
+// restart group g (ce = check_every), written on the device by the checks;
+// iteration t of the interval takes entry t + 1 and rebuilds its iterate
+// from entry t.  uni >= 0 says that every active column belongs to group
+// uni.  With pdl the step kernels after the interval's first are
+// programmatic dependents of their predecessor (not with timing events,
+// which sit between them).
 template <typename T>
 cudaError_t launch_iteration(const IterData<T>& d, const IterBufs<T>& b, int ld, int ncol,
                              const T* hal, int t, int ce, int uni, bool check, bool pdl, cudaStream_t s,
                              cudaEvent_t* ev /* 3 events or nullptr */);
+
+// One matrix's share of a joint iteration: its operator and iterate blocks,
+// the lane's leading dimension, active columns, check interval, single group
+// (or -1) and Halpern table, as launch_iteration takes them.
+template <typename T>
+struct IterPart {
+    IterData<T> d;
+    IterBufs<T> b;
+    int ld, ncol, ce, uni;
+    const T* hal;
+};
+
+// Matrices per joint step launch.
+constexpr int kMaxParts = 8;
+
+// Iteration t of the intervals of several matrices at once: the primal steps
+// of all parts in one launch, then their dual steps in one launch (one per
+// row-group width among the parts, and per kMaxParts parts).  Each part gets
+// exactly what launch_iteration gives it alone: its rows are taken by other
+// blocks, but each row by one row group of the same width, summing in the
+// same order.  With pdl, as in launch_iteration.
+template <typename T>
+cudaError_t launch_iteration_multi(const IterPart<T>* parts, int nparts, int t, bool check, bool pdl,
+                                   cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // checks (lpb_check.cu)

@@ -32,7 +32,7 @@ RC_BARRIER, RC_ROBUST = 0, 1
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",
            "lpb_result_device", "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_batch_free",
            "lpb_destroy", "lpb_last_error", "lpb_scaling_noalloc", "lpb_obbt_tighten", "lpb_get_tuning",
-           "lpb_set_tuning", "lpb_autotune", "lpb_tune_batch"]
+           "lpb_set_tuning", "lpb_autotune", "lpb_tune_batch", "lpb_solve_multi"]
 # every symbol include/lpb_serve.h declares
 SERVE_EXPORTS = ["lpb_server_default_options", "lpb_server_create", "lpb_server_attach", "lpb_server_submit",
                  "lpb_server_poll", "lpb_server_wait", "lpb_server_result", "lpb_server_results",
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
     lib.lpb_create.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Options), C.POINTER(vp)]
     lib.lpb_solve.argtypes = [vp, i32, vp, d, i64, vp, vp, C.POINTER(vp)]
     lib.lpb_solve_dev.argtypes = [vp, i32, vp, d, i64, vp, vp, C.POINTER(vp)]
+    lib.lpb_solve_multi.argtypes = [i32, vp, vp, vp, d, i64, vp]
     lib.lpb_result.argtypes = [vp, i32, C.POINTER(Result), vp, vp]
     lib.lpb_results.argtypes = [vp, vp]
     lib.lpb_result_device.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
@@ -159,7 +160,7 @@ def load(path: str = LIB_PATH):
     lib.lpb_server_stats_get.argtypes = [vp, C.POINTER(ServerStats)]
     lib.lpb_server_destroy.argtypes = [vp]
     lib.lpb_server_destroy.restype = None
-    for f in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results", "lpb_result_device",
+    for f in ("lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_solve_multi", "lpb_result", "lpb_results", "lpb_result_device",
               "lpb_batch_profile", "lpb_handle_info", "lpb_scaling", "lpb_scaling_noalloc", "lpb_server_create",
               "lpb_server_attach", "lpb_server_submit", "lpb_server_poll", "lpb_server_wait", "lpb_server_result",
               "lpb_server_results", "lpb_server_request_info", "lpb_server_release", "lpb_server_stats_get"):
@@ -221,6 +222,21 @@ def lpb_solve_dev(h, num_lps: int, specs_dev_ptr: int, tol: float, max_iter: int
     _check(load().lpb_solve_dev(h, int(num_lps), specs_dev_ptr, float(tol), int(max_iter), warm_x_dev_ptr,
                                 warm_y_dev_ptr, C.byref(b)))
     return b
+
+
+def lpb_solve_multi(handles, specs, tol: float, max_iter: int):
+    """handles: handle pointers; specs: one SPEC_DTYPE array per handle.
+    Returns one batch pointer per handle."""
+    k = len(handles)
+    sps = [np.ascontiguousarray(sp, dtype=SPEC_DTYPE) for sp in specs]
+    if len(sps) != k:
+        raise ValueError("one spec array per handle")
+    hv = (C.c_void_p * k)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    nv = (C.c_int32 * k)(*[int(sp.shape[0]) for sp in sps])
+    pv = (C.c_void_p * k)(*[sp.ctypes.data if sp.size else None for sp in sps])
+    out = (C.c_void_p * k)()
+    _check(load().lpb_solve_multi(k, hv, nv, pv, float(tol), int(max_iter), out))
+    return [C.c_void_p(out[i]) for i in range(k)]
 
 
 def lpb_result(b, lp: int, n: int, m: int, want_xy: bool = True):
@@ -481,6 +497,19 @@ class Handle:
                                       None if warm_y is None else warm_y.data_ptr()))
         b._num = num
         return b
+
+    @staticmethod
+    def solve_multi(handles, specs, tol: float = 1e-4, max_iter: int = 100000):
+        """Batches on several handles solved together (lpb_solve_multi):
+        specs[i] for handles[i]; one Batch per handle."""
+        sps = [sp if isinstance(sp, np.ndarray) else specs_from(sp) for sp in specs]
+        ptrs = lpb_solve_multi([h.ptr for h in handles], sps, tol, max_iter)
+        out = []
+        for h, sp, p in zip(handles, sps, ptrs):
+            b = Batch(h, p)
+            b._num = int(sp.shape[0])
+            out.append(b)
+        return out
 
     def info(self):
         return lpb_handle_info(self.ptr)
