@@ -552,6 +552,8 @@ def main():
     ap.add_argument("--workload", default="sb_large", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--extra-obbt", type=int, default=1,
                     help="also time the 1024-LP bound-tightening batch once (an extra key)")
+    ap.add_argument("--extra-joint", type=int, default=1,
+                    help="also time eight small matrices solved alone and as one joint solve (an extra key)")
     ap.add_argument("--requests", type=int, default=160, help="serving: requests in the timed Poisson stream")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate as a fraction of capacity")
     ap.add_argument("--priorities", type=int, default=1, help="serving: stream priorities by matrix size")
@@ -617,6 +619,10 @@ def main():
         if rank == 0 and not args.no_cpu_baseline and world == 1:
             extra["cpu_baseline"] = cpu_baseline(wo, "obbt_square", os.cpu_count() or 1, 0)
 
+    joint = None
+    if args.extra_joint and not args.no_extras and rank == 0:
+        joint = joint_extra(lpb, torch, args.seed)
+
     out = None
     if rank == 0:
         cores = os.cpu_count() or 1
@@ -645,6 +651,7 @@ def main():
             "setup_ms": m["setup_ms"],
             "polish": m["polish"],
             "obbt_square": extra,
+            "joint_solve": joint,
             "clocks": m["clocks"],
         }
     if dist:
@@ -652,6 +659,46 @@ def main():
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+JOINT_ROWS = (1000, 1250, 1500, 1750, 2000, 2250, 2500, 2750)
+JOINT_LPS = 32
+
+
+def joint_extra(lpb, torch, seed, reps=3):
+    """Eight small strong-branching matrices (power-law rows as sb_powerlaw,
+    m = 1000 .. 2750, n = 2m), 32 LPs each: solved one matrix after another
+    and as one joint solve (lpb_solve_multi: one primal and one dual step
+    launch per iteration for all eight).  LPs/s of both (best of two rounds
+    of `reps` solves each) and whether the joint results equal the alone
+    ones bitwise."""
+    mats = lpgen.serving_matrices(seed0=seed + 10, rows=JOINT_ROWS)
+    rng = np.random.default_rng(seed + 5)
+    specs = [lpgen.sb_specs(lp.x0, rng.choice(lp.n, size=JOINT_LPS // 2, replace=False)) for lp in mats]
+    hs = [lpb.Handle(lp, precision=lpb.MIXED) for lp in mats]
+    alone = lambda: [h.solve(sp, tol=TOL, max_iter=100000) for h, sp in zip(hs, specs)]
+    joint = lambda: lpb.Handle.solve_multi(hs, specs, tol=TOL, max_iter=100000)
+    ra, rj = alone(), joint()
+    same = all(np.array_equal(a.results(), j.results()) for a, j in zip(ra, rj))
+    best = {}
+    for _ in range(2):
+        for nm, f in (("alone", alone), ("joint", joint)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                bs = f()
+            torch.cuda.synchronize()
+            best[nm] = min(best.get(nm, 1e30), (time.perf_counter() - t) / reps)
+    lps = JOINT_LPS * len(mats)
+    solved = sum(int(np.sum(b.results()["status"] <= 2)) for b in bs)
+    return {"workload": f"{len(mats)} power-law SB matrices m={JOINT_ROWS[0]}..{JOINT_ROWS[-1]} n=2m, "
+                        f"{JOINT_LPS} LPs each, fp32-iterates/double-float-checks",
+            "lps": lps, "lps_solved": solved, "unit": UNIT,
+            "alone": {"value": solved / best["alone"], "ms": best["alone"] * 1e3,
+                      "step_launches_per_iteration": 2 * len(mats)},
+            "joint": {"value": solved / best["joint"], "ms": best["joint"] * 1e3, "step_launches_per_iteration": 2},
+            "speedup": best["alone"] / best["joint"], "bitwise_equal_to_alone": bool(same),
+            "timing": "wall clock of complete solves (host API, device-resident specs excluded), synchronized"}
 
 
 def measure(args, lpb, torch, w, name, dev, stream, flush, steps, warmup, dist, clocks, extras, check_oracle):
