@@ -201,6 +201,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def step_source_sha(csrc: str) -> str:
+    """Hash of the step kernels' source: their device code (lpb_step.h) and
+    their launches (lpb_iter.cu)."""
+    h = hashlib.sha256()
+    for f in ("lpb_step.h", "lpb_iter.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_name: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary and how they were
     taken, if they were taken on the current kernel source (else None)."""
@@ -210,10 +219,10 @@ def ncu_traffic(kernel_name: str, workload: str):
             d = json.load(f)
     except Exception:
         return None, None
-    src = os.path.join(ROOT, "paper_2601_21990_gb300", "csrc", "lpb_iter.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2601_21990_gb300", "csrc")
+    h = step_source_sha(csrc)
     ent = d.get(workload, {}).get(kernel_name)
-    if not ent or ent.get("lpb_iter_sha") != h:
+    if not ent or ent.get("step_source_sha") != h:
         return None, None
     return ent.get("dram_bytes_per_launch"), f"ncu DRAM bytes of one {ent.get('ncol')}-LP launch: {ent.get('note')}"
 
@@ -378,14 +387,7 @@ def oracle_error(w, name, batch, res):
 
 
 def run_serving(args, rank, world, local):
-    """Continuous batching over five matrices (m = 1k .. 200k, n = 2m, power-
-    law rows): first the capacity with every request queued at once, then a
-    seeded Poisson stream at args.load of that capacity; latency is each
-    request's submit-to-done time.  Every request warm-starts from its
-    matrix's base LP, solved first and kept on the device."""
     import torch
-
-    from paper_2601_21990_gb300 import lpb
 
     torch.cuda.set_device(local)
     dist = None
@@ -394,6 +396,22 @@ def run_serving(args, rank, world, local):
 
         dist_mod.init_process_group("nccl")
         dist = dist_mod
+    line = serving_measure(args, rank, world, local, dist, args.requests, args.warmup)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def serving_measure(args, rank, world, local, dist, requests, warmup):
+    """Continuous batching over five matrices (m = 1k .. 200k, n = 2m, power-
+    law rows): first the capacity with every request queued at once, then a
+    seeded Poisson stream at args.load of that capacity; latency is each
+    request's submit-to-done time.  Every request warm-starts from its
+    matrix's base LP, solved first and kept on the device.  Returns the
+    bench line on rank 0 (None elsewhere)."""
+    import torch
+
+    from paper_2601_21990_gb300 import lpb
+
     mats = lpgen.serving_matrices(seed0=args.seed + 10 * rank)
     # smaller matrices get more urgent streams: their short intervals take SMs
     # ahead of the large matrices' queued kernels
@@ -423,13 +441,13 @@ def run_serving(args, rank, world, local):
             solved += solved_count(res)
         return solved, d2h
 
-    warm = lpgen.serving_stream(mats, seed=99, count=max(args.warmup, 1) * 5)
+    warm = lpgen.serving_stream(mats, seed=99, count=max(warmup, 1) * 5)
     for r in [submit(k, sp) for _, k, sp in warm]:
         srv.wait(r)
         srv.release(r)
     # capacity: everything queued at once; the rate while 80% of the LPs
     # finish (the last few requests alone would measure their latency)
-    cap_stream = lpgen.serving_stream(mats, seed=101, count=max(args.requests // 2, 10))
+    cap_stream = lpgen.serving_stream(mats, seed=101, count=max(requests // 2, 10))
     cap_ids = [submit(k, sp) for _, k, sp in cap_stream]
     done = []
     for r in cap_ids:
@@ -446,7 +464,7 @@ def run_serving(args, rank, world, local):
         if acc >= 0.8 * tot:
             cap = acc / max(t_d - t_first, 1e-9)
             break
-    stream = lpgen.serving_stream(mats, seed=100, count=args.requests)
+    stream = lpgen.serving_stream(mats, seed=100, count=requests)
     mean_lps = float(np.mean([len(sp) for _, _, sp in stream]))
     rate = args.load * cap / mean_lps  # requests per second
     if dist:
@@ -481,9 +499,10 @@ def run_serving(args, rank, world, local):
     total_s = wall
     total_s, nsolved_all = reduce_over_ranks(dist, wall, nsolved, f"cuda:{local}")
     value = nsolved_all / total_s
+    line = None
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": args.warmup,
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": warmup,
             "ms_per_step": 1e3 * total_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_MIXED, "data": "synthetic",
             "config": {"workload": "serving: 5 power-law matrices m=1k..200k n=2m, Poisson requests of U{1..256} "
@@ -509,8 +528,9 @@ def run_serving(args, rank, world, local):
                     "what": "the serving API itself: host records in, host results out"},
             "gpu_launches": int(st1.kernels - st0.kernels),
             "clocks": clk,
-        }), flush=True)
+        }
     srv.close()
+    return line
 
 
 def cusparse_spmm(lp, ncol, dev, reps=20):
@@ -549,11 +569,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sb_large", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="sb_large", choices=sorted(WORKLOADS) + ["serving", "joint"])
     ap.add_argument("--extra-obbt", type=int, default=1,
                     help="also time the 1024-LP bound-tightening batch once (an extra key)")
     ap.add_argument("--extra-joint", type=int, default=1,
                     help="also time eight small matrices solved alone and as one joint solve (an extra key)")
+    ap.add_argument("--extra-serving", type=int, default=80,
+                    help="also run the serving workload with this many requests (an extra key; 0: skip)")
     ap.add_argument("--requests", type=int, default=160, help="serving: requests in the timed Poisson stream")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate as a fraction of capacity")
     ap.add_argument("--priorities", type=int, default=1, help="serving: stream priorities by matrix size")
@@ -571,14 +593,24 @@ def main():
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
-        if args.workload == "serving":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop; the reference "
-                              "arm runs on the batch workloads"}), flush=True)
+        if args.workload in ("serving", "joint"):
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop or joint solve; "
+                              "the reference arm runs on the batch workloads"}), flush=True)
             return
         run_reference(args, rank, world)
         return
     if args.workload == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "joint":
+        # the joint-solve comparison alone (its key of the default line)
+        import torch
+
+        from paper_2601_21990_gb300 import lpb
+
+        torch.cuda.set_device(local)
+        if rank == 0:
+            print(json.dumps({"workload": "joint", "joint_solve": joint_extra(lpb, torch, args.seed)}), flush=True)
         return
 
     import torch
@@ -622,6 +654,12 @@ def main():
     joint = None
     if args.extra_joint and not args.no_extras and rank == 0:
         joint = joint_extra(lpb, torch, args.seed)
+    # continuous batching (the serving workload), shortened: p50 / p99 latency
+    serving = None
+    if args.extra_serving > 0 and not args.no_extras and rank == 0 and world == 1:
+        sl = serving_measure(args, 0, 1, local, None, args.extra_serving, 3)
+        serving = {k: sl[k] for k in ("value", "unit", "ms_per_step", "config", "latency_ms", "latency_by_matrix",
+                                      "server", "e2e", "gpu_launches", "clocks")}
 
     out = None
     if rank == 0:
@@ -652,6 +690,7 @@ def main():
             "polish": m["polish"],
             "obbt_square": extra,
             "joint_solve": joint,
+            "serving": serving,
             "clocks": m["clocks"],
         }
     if dist:
@@ -689,6 +728,12 @@ def joint_extra(lpb, torch, seed, reps=3):
                 bs = f()
             torch.cuda.synchronize()
             best[nm] = min(best.get(nm, 1e30), (time.perf_counter() - t) / reps)
+    # one more joint solve inside the NVTX range the ncu captures select
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    joint()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     lps = JOINT_LPS * len(mats)
     solved = sum(int(np.sum(b.results()["status"] <= 2)) for b in bs)
     return {"workload": f"{len(mats)} power-law SB matrices m={JOINT_ROWS[0]}..{JOINT_ROWS[-1]} n=2m, "
