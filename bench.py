@@ -202,10 +202,11 @@ class ClockSampler:
 
 
 def step_source_sha(csrc: str) -> str:
-    """Hash of the step kernels' source: their device code (lpb_step.h) and
-    their launches (lpb_iter.cu)."""
+    """Hash of the step kernels' source: their device code (lpb_step.h),
+    their launches (lpb_iter.cu) and the long-row segments they take
+    (lpb_internal.h, lpb_setup.cu)."""
     h = hashlib.sha256()
-    for f in ("lpb_step.h", "lpb_iter.cu"):
+    for f in ("lpb_step.h", "lpb_iter.cu", "lpb_internal.h", "lpb_setup.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -68,7 +68,7 @@ struct Csr {
     int n_long = 0;
     int long_thr = kLongRow;    // rows longer than this get a whole block (tunable)
     int g_shift = 0;            // step kernels use (lanes per row from the batch width) >> g_shift
-    // Step kernels cut a long row into segments of at most kLongSeg entries,
+    // Step kernels cut a long row into segments of at most kStepSeg entries,
     // one block each, listed segment-major (every row's segment 0, then every
     // row's segment 1, ...) so that the blocks running together gather from
     // the same range of columns.  lseg[2 b], lseg[2 b + 1]: the long row
@@ -87,7 +87,18 @@ struct Csr {
 #ifndef LPB_LONG_SEG
 #define LPB_LONG_SEG 1024
 #endif
-constexpr int kLongSeg = LPB_LONG_SEG;  // entries per segment of a long row in the step kernels
+constexpr int kLongSeg = LPB_LONG_SEG;  // rows longer than this get a block in the power iteration
+// Entries per segment of a long row in the step kernels.  Segments are
+// listed segment-major, so the blocks resident together gather from a
+// window of columns about (resident blocks / long rows) segments wide: with
+// 256 entries that window of the gathered block fits in L2 on the large
+// strong-branching batch (500 rows of 10k entries), where 1024-entry
+// segments span twice the L2 (dual step 878 -> 844 ms per solve on GB300;
+// 512: 858 ms; 128: 889 ms, more blocks and partial sums).
+#ifndef LPB_STEP_SEG
+#define LPB_STEP_SEG 256
+#endif
+constexpr int kStepSeg = LPB_STEP_SEG;
 
 // Per-column parameters of the iteration kernels (structure of arrays,
 // length >= ld, in the iterate precision T).

@@ -528,7 +528,7 @@ cudaError_t transpose_csr(const Csr& a, const double* a_vals, Csr& at, int* perm
 }
 
 // Segments of the long rows for the step kernels: long row i (length len_i)
-// gets ceil(len_i / kLongSeg) segments; blocks are listed segment-major.
+// gets ceil(len_i / kStepSeg) segments; blocks are listed segment-major.
 static cudaError_t build_long_segments(Csr& a, cudaStream_t s) {
     cudaError_t e;
     if (a.n_long == 0) return cudaSuccess;
@@ -545,7 +545,7 @@ static cudaError_t build_long_segments(Csr& a, cudaStream_t s) {
     std::vector<int> seg0(a.n_long + 1, 0);
     int max_ns = 0;
     for (int i = 0; i < a.n_long; ++i) {
-        const int ns = std::max(1, (len[i] + kLongSeg - 1) / kLongSeg);
+        const int ns = std::max(1, (len[i] + kStepSeg - 1) / kStepSeg);
         seg0[i + 1] = seg0[i] + ns;
         max_ns = std::max(max_ns, ns);
     }

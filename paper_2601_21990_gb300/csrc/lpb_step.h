@@ -397,7 +397,7 @@ __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ dfloat add(dfloat a, dfloat b) { return a + b; }
 
 // One step (primal or dual) of the iteration on one column tile.
-//   Blocks [0, n_lblocks): one segment of a long row each (at most kLongSeg
+//   Blocks [0, n_lblocks): one segment of a long row each (at most kStepSeg
 //   entries), split into contiguous pieces over the block's row groups and
 //   reduced in shared memory.  A row of one segment is finished by its block;
 //   for a row of several, each block stores its partial sums, and the block

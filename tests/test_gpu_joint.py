@@ -50,7 +50,7 @@ def uneven_parts():
     """Four matrices of uneven size with batches of uneven width.  FP32 row
     groups: 6 LPs -> 2 lanes, 40 and 50 LPs -> 16 lanes (one launch holds
     both), 136 LPs -> 32 lanes over two column tiles with a ragged second;
-    the last matrix has four rows of 2500 entries (three segments each)."""
+    the last matrix has four rows of 2500 entries (ten segments each)."""
     a = lpgen.sb_small(seed=0)
     b = lpgen.sb_powerlaw(seed=3, m=3000, n=7000, children=64)
     c = lpgen.sb_small(seed=1)

@@ -451,8 +451,8 @@ def test_ragged_and_multi_tile_batches(lpb, orc):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_long_rows_in_segments_over_several_tiles(lpb, orc, precision):
-    """Rows longer than one segment (1024 entries) are split over several
-    blocks whose last one finishes the row.  Four rows of 2500 entries (three
+    """Rows longer than one segment (256 entries) are split over several
+    blocks whose last one finishes the row.  Four rows of 2500 entries (ten
     segments each) among rows of 3-8, 136 LPs (16 distinct children repeated:
     two column tiles of 128 FP32 LPs with a ragged second tile, three of 64
     FP64 LPs), with the default launch shape and with the lane shift 1 (more,
