@@ -356,14 +356,35 @@ __global__ void k_power_init(double* v, int n, uint64_t seed) {
 // block covers and the order of every sum are the same on every run.  The normalisation v = w / ||w|| is
 // applied after the forward product, u = (A~ w) / ||w||, so no launch writes
 // v and none only reduces.
+//
+// The short-row blocks of a launch: one per kPowRows rows, at least
+// kPowBlocks and at most kPowBlocksMax (a function of the row count alone,
+// so still the same on every run).  Each row group walks its rows one after
+// another, a chain of dependent loads per row: on the 1M x 2M strong-
+// branching matrix the fixed 512 blocks gave each row group 61 (A~) and
+// 122 (A~^T) rows; matrices of up to 131k rows keep 512 blocks, the best of
+// a sweep on the 20k-row and 100k-row matrices.
 #ifndef LPB_POW_BLOCKS
 #define LPB_POW_BLOCKS 512
+#endif
+#ifndef LPB_POW_BLOCKS_MAX
+#define LPB_POW_BLOCKS_MAX 4096
+#endif
+#ifndef LPB_POW_ROWS
+#define LPB_POW_ROWS 256
 #endif
 #ifndef LPB_POW_GROUP
 #define LPB_POW_GROUP 8
 #endif
 constexpr int kPowBlocks = LPB_POW_BLOCKS;
+constexpr int kPowBlocksMax = LPB_POW_BLOCKS_MAX;
+constexpr int kPowRows = LPB_POW_ROWS;
 constexpr int kPowThreads = 256;
+static_assert(kPowBlocks <= kPowBlocksMax, "power grid bounds");
+inline int pow_blocks(int rows) {
+    const long long b = ((long long)rows + kPowRows - 1) / kPowRows;
+    return (int)(b < kPowBlocks ? kPowBlocks : b > kPowBlocksMax ? kPowBlocksMax : b);
+}
 constexpr int kPowGroup = LPB_POW_GROUP;  // lanes per row
 static_assert(kPowGroup >= 1 && kPowGroup <= 32 && (kPowGroup & (kPowGroup - 1)) == 0, "lanes per row: a power of 2");
 
@@ -455,6 +476,11 @@ __global__ void __launch_bounds__(kPowThreads) k_power_norm(const double* __rest
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     finish_norm(part, ticket, nrm, nullptr, 0, sh);
 }
+
+// Blocks of the Ruiz and Pock-Chambolle row statistics (a warp per row, so
+// the grid changes no result): up to 16384, about 8 rows per warp on a
+// 1M-row matrix
+constexpr int kStatCap = 16384;
 
 inline int grid_for(long long work, int threads, int cap = 4096) {
     long long g = (work + threads - 1) / threads;
@@ -615,11 +641,11 @@ cudaError_t ruiz_pock_chambolle(const Csr& a, const double* a_vals, const Csr& a
         const bool pc = it >= ruiz_iters;
         // both statistics from the same A~, then both factors updated
         if (m > 0) {
-            if (pc) k_row_stat<true><<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
-            else k_row_stat<false><<<grid_for((long long)m * 32, 256), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
+            if (pc) k_row_stat<true><<<grid_for((long long)m * 32, 256, kStatCap), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
+            else k_row_stat<false><<<grid_for((long long)m * 32, 256, kStatCap), 256, 0, s>>>(a.rp, a.ci, a_vals, m, d_r, d_c, true, tmp_r);
         }
-        if (pc) k_row_stat<true><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
-        else k_row_stat<false><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
+        if (pc) k_row_stat<true><<<grid_for((long long)n * 32, 256, kStatCap), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
+        else k_row_stat<false><<<grid_for((long long)n * 32, 256, kStatCap), 256, 0, s>>>(at.rp, at.ci, at_vals, n, d_c, d_r, false, tmp_c);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (m > 0) k_apply_scale<<<grid_for(m, 256), 256, 0, s>>>(d_r, tmp_r, m);
         k_apply_scale<<<grid_for(n, 256), 256, 0, s>>>(d_c, tmp_c, n);
@@ -704,7 +730,7 @@ cudaError_t rhs_norm2(const double* ls, const double* us, int m, double* out_dev
 // (at most nnz / kLongSeg rows have more than kLongSeg entries: one block
 // and one norm partial each)
 size_t power_work_doubles(int m, int n, long long nnz, int max_iter) {
-    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocks + (size_t)(nnz / kLongSeg + 1) + 3 +
+    return (size_t)n + (size_t)(m > 0 ? m : 1) + (size_t)kPowBlocksMax + (size_t)(nnz / kLongSeg + 1) + 3 +
            2 * ((size_t)max_iter + 1);
 }
 
@@ -721,13 +747,13 @@ static cudaError_t power_iterate(const Csr& a, const Csr& at, const Csr& va, con
 cudaError_t power_norm(const Csr& a, const Csr& at, int max_iter, double tol, uint64_t seed, double* work,
                        double* est_out, int* iters_out, cudaStream_t s) {
     const int m = a.rows, n = a.cols;
-    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocks + nnz / kLongSeg + 1),
+    // work layout (power_work_doubles): w (n), u (m), part (kPowBlocksMax + nnz / kLongSeg + 1),
     // ||u||, ||w||, the ticket, hist_est, hist_nw (max_iter + 1 each); w starts as the
     // unnormalised start vector
     double* w = work;
     double* u = w + n;
     double* part = u + (m > 0 ? m : 1);
-    double* nrm_u = part + kPowBlocks + (size_t)a.nnz / kLongSeg + 1;
+    double* nrm_u = part + kPowBlocksMax + (size_t)a.nnz / kLongSeg + 1;
     double* nrm_w = nrm_u + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(nrm_w + 1);
     double* hist_est = nrm_w + 2;
@@ -777,10 +803,10 @@ static cudaError_t power_iterate(const Csr& a, const Csr& at, const Csr& va, con
         for (int it = base; it <= last; ++it) {
             // u = A~ w / ||w|| (records ||u||), then w = A~^T u (records ||w||)
             // rows of more than kLongSeg entries get a whole block each
-            k_power_spmv<<<va.n_long + kPowBlocks, kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, va.long_rows,
+            k_power_spmv<<<va.n_long + pow_blocks(m), kPowThreads, 0, s>>>(a.rp, a.ci, a.v64, m, va.long_rows,
                                                                           va.n_long, kLongSeg, w, nrm_w, u, part,
                                                                           ticket, nrm_u, hist_est, it);
-            k_power_spmv<<<vat.n_long + kPowBlocks, kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, vat.long_rows,
+            k_power_spmv<<<vat.n_long + pow_blocks(n), kPowThreads, 0, s>>>(at.rp, at.ci, at.v64, n, vat.long_rows,
                                                                            vat.n_long, kLongSeg, u, nullptr, w, part,
                                                                            ticket, nrm_w, hist_nw, it);
         }
