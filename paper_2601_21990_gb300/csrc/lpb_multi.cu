@@ -15,13 +15,14 @@
 
 #include "lpb_step.h"
 
-#ifndef MULTI_MB_F
-#define MULTI_MB_F 8
+// resident blocks per SM of the joint kernels with row groups of 8 or more
+// lanes, FP32 and FP64 (see MultiMinBlocks)
+#ifndef LPB_MULTI_MIN_BLOCKS_F32
+#define LPB_MULTI_MIN_BLOCKS_F32 8
 #endif
-#ifndef MULTI_MB_D
-#define MULTI_MB_D 7
+#ifndef LPB_MULTI_MIN_BLOCKS_F64
+#define LPB_MULTI_MIN_BLOCKS_F64 7
 #endif
-#define MULTI_MB_T(T, G) (G <= 4 ? 5 : std::is_same<T, float>::value ? MULTI_MB_F : MULTI_MB_D)
 
 namespace lpb {
 
@@ -43,9 +44,13 @@ static_assert(sizeof(MultiStepArgs<double>) <= 4096, "joint step arguments excee
 
 // Resident blocks per SM of the joint kernels: those the single-matrix
 // kernels reach with their register counts (the part lookup and the
-// indexed arguments cost the joint kernels a few registers more)
+// indexed arguments cost the joint kernels a few registers more).  Row
+// groups of 4 lanes or fewer keep the single kernels' bound, where the
+// tighter cap would spill.
 template <typename T, int G, bool PRIMAL> struct MultiMinBlocks {
-    static constexpr int v = (MinBlocks<T, G, PRIMAL>::v > MULTI_MB_T(T, G) ? MinBlocks<T, G, PRIMAL>::v : MULTI_MB_T(T, G));
+    static constexpr int cap = G <= 4 ? 5 : std::is_same<T, float>::value ? LPB_MULTI_MIN_BLOCKS_F32
+                                                                           : LPB_MULTI_MIN_BLOCKS_F64;
+    static constexpr int v = MinBlocks<T, G, PRIMAL>::v > cap ? MinBlocks<T, G, PRIMAL>::v : cap;
 };
 
 template <typename T, int G, bool CHECK, bool PRIMAL>
