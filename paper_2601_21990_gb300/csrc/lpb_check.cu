@@ -1035,6 +1035,12 @@ __global__ void __launch_bounds__(32 * kReduceRows, 4)
     const int kind = a.col.kind[jj], var = a.col.var[jj];
     const df olo = df_from(a.col.lo[jj]), ohi = df_from(a.col.hi[jj]), oc = df_from(a.col.c[jj]);
     for (int i = blockIdx.x * kReduceRows + threadIdx.y; i < a.n; i += gridDim.x * kReduceRows) {
+        // the row's own operands, issued before its gathers so that their
+        // round trip overlaps the gathers' rather than following them
+        const size_t off = (size_t)i * a.ld + jj;
+        const TI xh = a.Xh[off];
+        const TI dx = a.DX[off];
+        const TI x0 = a.X0[off];
         // A~^T [y^, Pi_B(dy), dy] for row i, column j: the gathers of four
         // entries are issued together (loads in flight), the sums still taken
         // in entry order
@@ -1073,12 +1079,10 @@ __global__ void __launch_bounds__(32 * kReduceRows, 4)
         q0 = quick_two_sum(q0.hi, q0.lo);
         q1 = quick_two_sum(q1.hi, q1.lo);
         q2 = quick_two_sum(q2.hi, q2.lo);
-        const size_t off = (size_t)i * a.ld + jj;
         const df dc = a.dc[i], idc = a.idc[i];
         df cj = a.c[i], lo = a.xl[i], hi = a.xu[i];
         if (kind == 2) cj = var == i ? oc : df_zero();
         else if (kind == 1 && var == i) { lo = olo; hi = ohi; }
-        const TI xh = a.Xh[off];
         const df x = df_clamp(it_mul(dc, xh), lo, hi);
         const df q = df_add(cj, df_mul(q0, idc));                    // c + A^T y
         const df r = df_barrier(df_neg(q), lo, hi);                  // reduced cost
@@ -1089,10 +1093,9 @@ __global__ void __launch_bounds__(32 * kReduceRows, 4)
         f_c2 += cj.hi * cj.hi;
         df_acc(d_ctx, df_mul(cj, x));
         df_acc(d_phr, df_support(rs, lo, hi));
-        const TI dx = a.DX[off];
         const float dxs = it_f(dx);
         f_dx2 += dxs * dxs;
-        const float dx0 = it_diff(a.restart_to_output ? xh : a.X[off], a.X0[off]);
+        const float dx0 = it_diff(a.restart_to_output ? xh : a.X[off], x0);
         f_dx02 += dx0 * dx0;
         // A^T y^k = A^T y^ - A^T (y^ - y^k)
         const df gk = df_mul(df_sub(q0, q2), idc);
