@@ -27,6 +27,7 @@ STATUS_NAMES = ["OPTIMAL", "PRIMAL_INFEASIBLE", "DUAL_INFEASIBLE", "ITERATION_LI
 FP64, MIXED = 0, 1
 POLISH_DFLOAT, POLISH_FP64 = 0, 1
 RC_BARRIER, RC_ROBUST = 0, 1
+LPB_MAX_JOINT = 64  # most handles in one lpb_solve_multi call
 
 # every symbol include/lpb.h declares
 EXPORTS = ["lpb_default_options", "lpb_create", "lpb_solve", "lpb_solve_dev", "lpb_result", "lpb_results",

@@ -164,3 +164,22 @@ def test_host_validation_rejects_bad_csr(lib):
         with pytest.raises(lpb.LpbError) as e:
             lpb.lpb_create(**kw)
         assert e.value.code == lpb.LPB_ERR_INVALID_ARG, b
+
+
+def test_joint_solve_argument_checks_need_no_device(lib):
+    """lpb_solve_multi rejects a bad count or NULL arrays before any device
+    call (and sets the last error), so these run without a GPU."""
+    import ctypes as C
+
+    from paper_2601_21990_gb300 import lpb
+
+    out = (C.c_void_p * 2)()
+    hv = (C.c_void_p * 2)()
+    nv = (C.c_int32 * 2)(1, 1)
+    pv = (C.c_void_p * 2)()
+    cases = [(0, hv, nv, pv, out), (lpb.LPB_MAX_JOINT + 1, hv, nv, pv, out), (1, None, nv, pv, out),
+             (1, hv, None, pv, out), (1, hv, nv, None, out), (1, hv, nv, pv, None), (2, hv, nv, pv, out)]
+    for k, h, n, p, o in cases:
+        assert lib.lpb_solve_multi(k, h, n, p, 1e-4, 100, o) == lpb.LPB_ERR_INVALID_ARG, k
+        assert lib.lpb_last_error()
+    assert lib.lpb_solve_multi(1, hv, nv, pv, 0.0, 100, out) == lpb.LPB_ERR_INVALID_ARG  # tol
