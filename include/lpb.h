@@ -21,9 +21,12 @@
  *  - Indices are 0-based.  CSR row_ptr has m+1 entries, row_ptr[0] == 0.
  *  - Every function returns an lpb_err; the library never aborts, traps or
  *    prints.  lpb_last_error() gives a message for the calling thread.
- *  - A handle is not thread-safe; distinct handles are independent.
+ *  - A handle is not thread-safe; distinct handles are independent.  The
+ *    handles of one lpb_solve_multi call are used by that call until it
+ *    returns.
  *  - All device work of a handle runs on the stream given in lpb_options
- *    (NULL: a stream the handle creates and owns).
+ *    (NULL: a stream the handle creates and owns), except the joint
+ *    intervals of lpb_solve_multi, which run on its first handle's stream.
  */
 #ifndef LPB_H
 #define LPB_H
