@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -179,11 +180,105 @@ lpb_err solve_impl(lpb_ctx* h, int num_lps, const lpb_lp_spec* specs_dev, double
     return LPB_OK;
 }
 
+// Joint intervals over the lanes of precision prec of the handles idx, on
+// stream s, until each of their groups is done or (can_stall) has stalled.
+// Groups whose next interval has the same length share one joint interval;
+// near the iteration cap, groups that reached it from different iteration
+// counts need intervals of different lengths.  So every group runs the
+// intervals it would run alone.
+template <typename T>
+lpb_err joint_loop(const std::vector<lpb_ctx*>& hs, int prec, std::vector<GroupRun>& g,
+                   std::vector<std::vector<GroupRun*>>& groups, std::vector<lpb_batch*>& bts,
+                   const std::vector<char>& can_stall, const std::vector<int>& idx, int64_t max_iter,
+                   cudaStream_t s) {
+    std::map<int, JointGraph> graphs;  // by interval length
+    std::vector<int> act, len, lens;
+    std::vector<lpb_ctx*> ah;
+    std::vector<Lane*> al;
+    std::vector<int> sc;
+    std::vector<lpb_profile*> ap;
+    lpb_err rc = LPB_OK;
+    while (rc == LPB_OK) {
+        act.clear();
+        len.clear();
+        for (int i : idx)
+            if (g[i].live > 0 && !(can_stall[i] && g[i].stalled)) {
+                act.push_back(i);
+                len.push_back((int)std::min<int64_t>(hs[i]->opt.check_every, max_iter - g[i].K));
+            }
+        if (act.empty()) break;
+        lens = len;
+        std::sort(lens.begin(), lens.end());
+        lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
+        for (int L : lens) {
+            ah.clear();
+            al.clear();
+            sc.clear();
+            ap.clear();
+            for (size_t a = 0; a < act.size(); ++a)
+                if (len[a] == L) {
+                    const int i = act[a];
+                    ah.push_back(hs[i]);
+                    al.push_back(&hs[i]->lane[prec]);
+                    sc.push_back(can_stall[i] ? hs[i]->opt.polish_stall_checks : 0);
+                    ap.push_back(&bts[i]->prof);
+                }
+            if ((rc = joint_interval<T>(ah.data(), al.data(), sc.data(), (int)ah.size(), L, s, graphs[L], ap.data())) !=
+                LPB_OK)
+                break;
+        }
+        if (rc != LPB_OK) break;
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "joint solve: interval");
+            break;
+        }
+        for (int i : act)
+            if ((rc = lane_collect<T>(hs[i], hs[i]->lane[prec], groups[i], s, &bts[i]->prof, true)) != LPB_OK) break;
+    }
+    for (auto& kv : graphs) joint_graph_free(kv.second);
+    return rc;
+}
+
+// Joint polish: the groups idx, stalled on their handles' FP32 lanes, move to
+// the polish lanes (iterate type TD) with their restart state (k, r0, w, ...)
+// and continue together in joint intervals, as polish_group runs each alone.
+template <typename TD>
+lpb_err polish_joint(const std::vector<lpb_ctx*>& hs, std::vector<GroupRun>& g,
+                     std::vector<std::vector<GroupRun*>>& groups, std::vector<lpb_batch*>& bts,
+                     const std::vector<int>& idx, int64_t max_iter, cudaStream_t s) {
+    constexpr int pp = std::is_same<TD, dfloat>::value ? kPrecDfl : kPrecF64;
+    const int count = (int)hs.size();
+    std::vector<std::vector<GroupRun*>> pg(count, std::vector<GroupRun*>(1, nullptr));
+    const std::vector<char> no_stall(count, 0);
+    std::vector<int> moved;
+    lpb_err rc = LPB_OK;
+    for (int i : idx) {
+        lpb_ctx* h = hs[i];
+        Lane& ln = h->lane[kPrecF32];
+        Lane& pl = h->lane[pp];
+        bts[i]->prof.kernels += 5;
+        bts[i]->prof.fp64_switch_iter = g[i].K;
+        if ((rc = lane_reserve(h, pl, pp, ln.cap, 1)) != LPB_OK) break;
+        moved.push_back(i);
+        if ((rc = lane_migrate<TD>(h, ln, pl, g[i], 0, 0, s, groups[i])) != LPB_OK) break;
+        pg[i][0] = &g[i];
+    }
+    if (rc == LPB_OK) rc = joint_loop<TD>(hs, pp, g, pg, bts, no_stall, moved, max_iter, s);
+    if (rc != LPB_OK)
+        for (int i : moved) {
+            Lane& pl = hs[i]->lane[pp];
+            pl.ncol = 0;
+            cudaMemsetAsync(pl.ctl, 0, sizeof(Control) * pl.gcap, s);
+        }
+    return rc;
+}
+
 // A joint solve: batch i is one restart group on the lane of handle hs[i]
 // (specs_dev[i] on that handle's device memory).  The lanes step together,
 // one joint interval after another on the first handle's stream, until
-// every batch is done or has stalled at FP32 resolution; a stalled batch
-// then polishes alone on its own handle.
+// every batch is done or has stalled at FP32 resolution; the stalled
+// batches then polish together on their handles' polish lanes.
 template <typename T>
 lpb_err solve_joint_impl(const std::vector<lpb_ctx*>& hs, const int32_t* num_lps,
                          const std::vector<const lpb_lp_spec*>& specs_dev, double tol, int64_t max_iter,
@@ -227,46 +322,21 @@ lpb_err solve_joint_impl(const std::vector<lpb_ctx*>& hs, const int32_t* num_lps
         rc = lane_admit<T>(h, ln, gi, specs_dev[i], nullptr, nullptr, n, m, tol, h->stream, groups[i]);
         can_stall[i] = std::is_same<T, float>::value && polish_enabled(h);
     }
-    JointGraph jg;
-    std::vector<int> act;
-    std::vector<lpb_ctx*> ah;
-    std::vector<Lane*> al;
-    std::vector<int> sc;
-    std::vector<lpb_profile*> ap;
-    while (rc == LPB_OK) {
-        act.clear();
-        for (int i = 0; i < count; ++i)
-            if (g[i].live > 0 && !(can_stall[i] && g[i].stalled)) act.push_back(i);
-        if (act.empty()) break;
-        // the active groups started together and ran the same intervals: one K
-        const int L = (int)std::min<int64_t>(hs[act[0]]->opt.check_every, max_iter - g[act[0]].K);
-        ah.clear();
-        al.clear();
-        sc.clear();
-        ap.clear();
-        for (int i : act) {
-            ah.push_back(hs[i]);
-            al.push_back(&hs[i]->lane[prec]);
-            sc.push_back(can_stall[i] ? hs[i]->opt.polish_stall_checks : 0);
-            ap.push_back(&bts[i]->prof);
-        }
-        if ((rc = joint_interval<T>(ah.data(), al.data(), sc.data(), (int)act.size(), L, s, jg, ap.data())) != LPB_OK)
-            break;
-        const cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "joint solve: interval");
-            break;
-        }
-        for (int i : act)
-            if ((rc = lane_collect<T>(hs[i], hs[i]->lane[prec], groups[i], s, &bts[i]->prof, true)) != LPB_OK) break;
-    }
-    joint_graph_free(jg);
+    std::vector<int> all;
+    for (int i = 0; i < count; ++i) all.push_back(i);
+    if (rc == LPB_OK) rc = joint_loop<T>(hs, prec, g, groups, bts, can_stall, all, max_iter, s);
     if (rc == LPB_OK) {
         const cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "joint solve");
     }
-    for (int i = 0; i < count && rc == LPB_OK; ++i)
-        if (g[i].live > 0) rc = polish_group(hs[i], hs[i]->lane[prec], g[i], groups[i], bts[i]->prof);
+    if (rc == LPB_OK && std::is_same<T, float>::value) {
+        // the batches still live have stalled: polish, by polish arithmetic
+        std::vector<int> dfl, f64;
+        for (int i = 0; i < count; ++i)
+            if (g[i].live > 0) (polish_dfloat(hs[i]) ? dfl : f64).push_back(i);
+        if (!dfl.empty()) rc = polish_joint<dfloat>(hs, g, groups, bts, dfl, max_iter, s);
+        if (rc == LPB_OK && !f64.empty()) rc = polish_joint<double>(hs, g, groups, bts, f64, max_iter, s);
+    }
     for (int i = 0; i < count; ++i) {
         lpb_ctx* h = hs[i];
         Lane& ln = h->lane[prec];
@@ -278,6 +348,10 @@ lpb_err solve_joint_impl(const std::vector<lpb_ctx*>& hs, const int32_t* num_lps
         }
         const cudaError_t e = cudaStreamSynchronize(h->stream);
         if (rc == LPB_OK && e != cudaSuccess) rc = cuda_fail(e, "joint solve");
+    }
+    if (rc == LPB_OK) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "joint solve");
     }
     return rc;
 }

@@ -731,6 +731,8 @@ template lpb_err joint_interval<float>(lpb_ctx* const*, Lane* const*, const int*
                                        JointGraph&, lpb_profile* const*);
 template lpb_err joint_interval<double>(lpb_ctx* const*, Lane* const*, const int*, int, int, cudaStream_t,
                                         JointGraph&, lpb_profile* const*);
+template lpb_err joint_interval<dfloat>(lpb_ctx* const*, Lane* const*, const int*, int, int, cudaStream_t,
+                                        JointGraph&, lpb_profile* const*);
 template lpb_err lane_migrate<double>(lpb_ctx*, Lane&, Lane&, GroupRun&, int, int, cudaStream_t,
                                       std::vector<GroupRun*>&);
 template lpb_err lane_migrate<dfloat>(lpb_ctx*, Lane&, Lane&, GroupRun&, int, int, cudaStream_t,

@@ -23,6 +23,11 @@
 #ifndef LPB_MULTI_MIN_BLOCKS_F64
 #define LPB_MULTI_MIN_BLOCKS_F64 7
 #endif
+// the double-float joint kernels (the joint polish phase): one block fewer
+// than the single kernels, whose 72 registers the part lookup would overflow
+#ifndef LPB_MULTI_MIN_BLOCKS_DF
+#define LPB_MULTI_MIN_BLOCKS_DF 6
+#endif
 
 namespace lpb {
 
@@ -51,6 +56,9 @@ template <typename T, int G, bool PRIMAL> struct MultiMinBlocks {
     static constexpr int cap = G <= 4 ? 5 : std::is_same<T, float>::value ? LPB_MULTI_MIN_BLOCKS_F32
                                                                            : LPB_MULTI_MIN_BLOCKS_F64;
     static constexpr int v = MinBlocks<T, G, PRIMAL>::v > cap ? MinBlocks<T, G, PRIMAL>::v : cap;
+};
+template <int G, bool PRIMAL> struct MultiMinBlocks<dfloat, G, PRIMAL> {
+    static constexpr int v = LPB_MULTI_MIN_BLOCKS_DF;
 };
 
 template <typename T, int G, bool CHECK, bool PRIMAL>
@@ -159,5 +167,6 @@ cudaError_t launch_iteration_multi(const IterPart<T>* parts, int nparts, int t, 
 
 template cudaError_t launch_iteration_multi<float>(const IterPart<float>*, int, int, bool, bool, cudaStream_t);
 template cudaError_t launch_iteration_multi<double>(const IterPart<double>*, int, int, bool, bool, cudaStream_t);
+template cudaError_t launch_iteration_multi<dfloat>(const IterPart<dfloat>*, int, int, bool, bool, cudaStream_t);
 
 }  // namespace lpb

@@ -125,19 +125,44 @@ def test_joint_solve_over_more_than_one_launch_of_parts(lpb, graphs, pdl):
 
 
 def test_joint_solve_with_polish(lpb):
-    """Batches that stall leave the joint launches and finish in the
-    double-float polish phase on their own handles, bitwise as alone.  The
-    first handle stalls after one check without halving (as the polish test
-    of the single solve forces it), the second keeps the default."""
-    ws = [lpgen.sb_small(seed=3), lpgen.sb_small(seed=2)]
+    """Batches that stall leave the joint FP32 launches and polish together
+    in joint launches on their handles' polish lanes, bitwise as alone.  Two
+    handles stall after one check without halving (as the polish test of the
+    single solve forces it) and polish in double-float together, a third
+    polishes in native FP64, a fourth keeps the defaults."""
+    ws = [lpgen.sb_small(seed=3), lpgen.sb_small(seed=4), lpgen.sb_small(seed=5), lpgen.sb_small(seed=2)]
     hs = [lpb.Handle(ws[0].lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1),
-          lpb.Handle(ws[1].lp, precision=lpb.MIXED)]
+          lpb.Handle(ws[1].lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1),
+          lpb.Handle(ws[2].lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1,
+                     polish_arith=lpb.POLISH_FP64),
+          lpb.Handle(ws[3].lp, precision=lpb.MIXED)]
     alone = [h.solve(w.specs, tol=1e-6, max_iter=200000) for h, w in zip(hs, ws)]
-    assert alone[0].profile().fp64_switch_iter >= 64
+    for a in alone[:3]:
+        assert a.profile().fp64_switch_iter >= 64
     joint = lpb.Handle.solve_multi(hs, [w.specs for w in ws], tol=1e-6, max_iter=200000)
     for a, j in zip(alone, joint):
         assert a.profile().fp64_switch_iter == j.profile().fp64_switch_iter
         assert_same(lpb, a, j)
+
+
+def test_joint_polish_near_the_iteration_cap(lpb):
+    """The polish phase up to an iteration cap that is not a multiple of the
+    check interval (1000 = 15 * 64 + 40): the last joint interval is 40
+    iterations long, and each batch stops at the cap as it does alone
+    (bitwise), with the LPs still iterating reported at the limit."""
+    ws = [lpgen.sb_small(seed=3), lpgen.sb_small(seed=4)]
+    hs = [lpb.Handle(ws[0].lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=1),
+          lpb.Handle(ws[1].lp, precision=lpb.MIXED, fp64_polish=1, polish_stall_checks=2)]
+    cap = 1000
+    alone = [h.solve(w.specs, tol=1e-11, max_iter=cap) for h, w in zip(hs, ws)]
+    joint = lpb.Handle.solve_multi(hs, [w.specs for w in ws], tol=1e-11, max_iter=cap)
+    hit = 0
+    for a, j in zip(alone, joint):
+        assert_same(lpb, a, j)
+        res = j.results()
+        assert np.all(res["iters"] <= cap)
+        hit += int(np.sum(res["status"] == lpb.ITERATION_LIMIT))
+    assert hit > 0
 
 
 def test_joint_solve_argument_errors(lpb):
