@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "lpb_joint_grid.h"
 #include "lpb_step.h"
 
 // resident blocks per SM of the joint kernels with row groups of 8 or more
@@ -64,11 +65,8 @@ template <int G, bool PRIMAL> struct MultiMinBlocks<dfloat, G, PRIMAL> {
 template <typename T, int G, bool CHECK, bool PRIMAL>
 __global__ void __launch_bounds__(kBlock, (MultiMinBlocks<T, G, PRIMAL>::v))
     k_step_multi(const __grid_constant__ MultiStepArgs<T> m) {
-    const int b = (int)blockIdx.x;
-    int p = 0;
-    while (p + 1 < m.nparts && b >= m.block0[p + 1]) ++p;
-    const int local = b - m.block0[p], gx = m.gx[p];
-    step_body<T, G, CHECK, PRIMAL>(m.part[p], local % gx, local / gx, gx);
+    const JointPlace q = joint_place((int)blockIdx.x, m.nparts, m.block0, m.gx);
+    step_body<T, G, CHECK, PRIMAL>(m.part[q.part], q.bx, q.by, q.gx);
 }
 
 // Each part gets the grid k_step would get for it alone: its long-row
@@ -84,18 +82,16 @@ cudaError_t launch_multi_k(MultiStepArgs<T>& m, bool pdl, cudaStream_t s) {
     int sms = 0, per_sm = 0;
     const cudaError_t e = launch_shape(shape, k_step_multi<T, G, CHECK, PRIMAL>, &sms, &per_sm);
     if (e != cudaSuccess) return e;
-    long long total = 0;
+    int nlb[kMaxParts], need[kMaxParts], tiles[kMaxParts];
     for (int p = 0; p < m.nparts; ++p) {
         StepArgs<T>& a = m.part[p];
-        const int need = (a.rows + GPB - 1) / GPB;
-        const int persist = need < sms * per_sm ? need : sms * per_sm;
         a.pdl = pdl ? 1 : 0;
-        m.gx[p] = a.n_lblocks + persist;
-        m.block0[p] = (int)total;
-        total += (long long)m.gx[p] * ((a.ncol + TN - 1) / TN);
-        if (total > INT_MAX) return cudaErrorInvalidConfiguration;
+        nlb[p] = a.n_lblocks;
+        need[p] = (a.rows + GPB - 1) / GPB;
+        tiles[p] = (a.ncol + TN - 1) / TN;
     }
-    m.block0[m.nparts] = (int)total;
+    const long long total = joint_layout(m.nparts, nlb, need, tiles, sms * per_sm, m.block0, m.gx);
+    if (total < 0) return cudaErrorInvalidConfiguration;
     if (total == 0) return cudaSuccess;
     return launch_with(k_step_multi<T, G, CHECK, PRIMAL>, dim3((unsigned)total), m, pdl, s);
 }

@@ -35,3 +35,18 @@ def test_graph_key_changes_with_every_baked_input(tmp_path):
                            os.path.join(ROOT, "tests", "native", "graph_key_test.cu"), "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout[-2000:]
+
+
+def test_joint_launch_grid_covers_each_part_once(tmp_path):
+    """The flattened grid of a joint step launch (several matrices in one
+    launch): every block falls in one part's own grid, every place of every
+    part is taken exactly once, in k_step's block order, and a grid past
+    INT_MAX blocks is rejected (seeded random mixes of up to 8 parts)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "joint_grid_test"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2601_21990_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "native", "joint_grid_test.cu"), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout[-2000:]
