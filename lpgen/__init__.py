@@ -295,6 +295,30 @@ def sb_large(seed: int = 0, m: int = 1000000, n: int = 2000000, dense_rows: int 
                     f"sb_large m={m} n={n} B={children} fp32-iterates/double-float-checks")
 
 
+def sb_dense_cols(seed: int = 0, m: int = 3000, n: int = 2000, dense_cols: int = 12, children: int = 16) -> Workload:
+    """m=3000, n=2000: columns of U{3..8} distinct rows, plus ``dense_cols``
+    columns of 40 .. 1500 rows (evenly spaced), so that rows of A^T exceed the
+    32-entry long-row threshold and the longest spans several 256-entry
+    segments; values sign*U[0.1,10]; x0 ~ U[0,10]^n, box [0,10]; l, u =
+    A x0 -/+ U[0,1]; c ~ N(0,1); 16 strong-branching children on 8 columns,
+    two of them dense."""
+    rng = np.random.default_rng(seed)
+    col_len = rng.integers(3, 9, size=n).astype(np.int64)
+    dense = rng.choice(n, size=dense_cols, replace=False)
+    col_len[dense] = np.linspace(40, 1500, dense_cols).astype(np.int64)
+    row_idx = _distinct_cols_per_row(rng, col_len, m).astype(np.int64)
+    vals = _signed_uniform(rng, row_idx.shape[0])
+    row_ptr, col_idx, v = _csc_to_csr(m, n, col_len, row_idx, vals)
+    x0 = rng.uniform(0.0, 10.0, size=n)
+    lp = LPData(m, n, row_ptr, col_idx, v, rng.standard_normal(n), None, None,
+                np.zeros(n), np.full(n, 10.0), x0, "sb_dense_cols")
+    _rows_around(lp, x0, rng)
+    others = np.setdiff1d(np.arange(n), dense)
+    cand = np.concatenate([dense[-2:], rng.choice(others, size=children // 2 - 2, replace=False)])
+    return Workload(lp, sb_specs(x0, cand), "mixed",
+                    f"sb_dense_cols m={m} n={n} B={children} ({dense_cols} columns of 40-1500 rows)")
+
+
 def covering_large_bounds(seed: int = 0, m: int = 300, n: int = 500, big: float = 1e10) -> Workload:
     """Covering LP whose variable boxes are mostly far larger than any
     optimum reaches, the case the reduced cost robust to large bounds is for:

@@ -479,6 +479,23 @@ def test_long_rows_in_segments_over_several_tiles(lpb, orc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dense_columns_long_rows_of_the_transpose(lpb, orc, precision):
+    """Columns of A longer than the long-row threshold: twelve columns of 40
+    to 1500 rows, so rows of A~^T take the primal step's long-row blocks (the
+    longest over six 256-entry segments), and for FP32 iterates the check
+    forms the A~^T products separately (k_spmm_df, k_reduce_n_df) instead of
+    inside the n-side reduction.  Two of the branched variables are dense
+    columns (overrides applied in the long-row epilogue); every LP against
+    the oracle, statuses (optimal and primal infeasible) included."""
+    w = lpgen.sb_dense_cols(seed=2)
+    ref = oracle_ref(orc, w.lp, w.specs)
+    assert np.sum(ref.status == 0) >= 4 and np.sum(ref.status == 1) >= 4
+    h = lpb.Handle(w.lp, precision=lpb.FP64 if precision == "fp64" else lpb.MIXED)
+    b = h.solve(w.specs, tol=GPU_TOL, max_iter=200000)
+    assert_parity(orc, w.lp, w.specs, b, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_halpern_trajectory_closed_form(lpb, precision):
     """The iteration itself, not only its limit: one variable, no rows, box
     [-1, 1], cost 1e-3, so eta = 0.998, w = 1 and T(z) = z - delta with
