@@ -108,6 +108,20 @@ def test_joint_solve_against_the_oracle(lpb, orc, precision):
             assert max(k["rel_primal"], k["rel_dual"], k["rel_gap"]) <= KKT_TOL, (lp.name, q, k)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_joint_solve_with_dense_columns(lpb, precision):
+    """A matrix whose columns exceed the long-row threshold (rows of A~^T of
+    40 to 1500 entries, over several segments) beside a small one: the joint
+    primal launch takes the long-row blocks of A~^T; bitwise as alone."""
+    parts = [(lpgen.sb_dense_cols(seed=2), 16), (lpgen.sb_small(seed=6), 40)]
+    lps = [(w.lp, w.specs.subset(np.arange(k) % len(w.specs))) for w, k in parts]
+    hs = [lpb.Handle(lp, precision=_prec(lpb, precision)) for lp, _ in lps]
+    alone = [h.solve(sp, tol=GPU_TOL, max_iter=200000) for h, (_, sp) in zip(hs, lps)]
+    joint = lpb.Handle.solve_multi(hs, [sp for _, sp in lps], tol=GPU_TOL, max_iter=200000)
+    for a, j in zip(alone, joint):
+        assert_same(lpb, a, j)
+
+
 @pytest.mark.parametrize("graphs,pdl", [(1, 1), (0, 1), (0, 0)])
 def test_joint_solve_over_more_than_one_launch_of_parts(lpb, graphs, pdl):
     """Ten matrices of one row-group width: two launches per step (eight
